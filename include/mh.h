@@ -1,0 +1,217 @@
+/*
+ * mh.h - C ABI of the GB300 (sm_103a) SdBG construction library.
+ *
+ * The library builds the succinct de Bruijn graph (SdBG) of MEGAHIT
+ * (Li, Liu, Luo, Sadakane & Lam, "MEGAHIT: an ultra-fast single-node solution
+ * for large and complex metagenomics assembly via succinct de Bruijn graph",
+ * 2015) from short reads, in four calls that follow the paper's Sec. 2:
+ *
+ *   mh_pack_reads   reads -> 2-bit codes                (implied by the 2kt-bit
+ *                   store of k-mers in Sec. 2, first paragraph)
+ *   mh_count_kmers  all (k+1)-mers on both strands, sorted and counted; those
+ *                   seen at least d times are solid      (Sec. 2, third para.)
+ *   mh_mercy_kmers  mercy (k+1)-mers between a solid edge without outdegree
+ *                   and a solid edge without indegree    (Sec. 2, third para.)
+ *   mh_build_sdbg   edges sorted in reverse-lexicographic (colex) order of
+ *                   their k-prefix, emitted as the BOSS arrays W (minus flag),
+ *                   last, F, the validity bit-vector and the zero-indegree
+ *                   store                                 (Sec. 2, first and
+ *                                                          second paragraphs)
+ *
+ * All arithmetic is integer and exact.
+ *
+ * Conventions
+ * -----------
+ * Symbols: A=0, C=1, G=2, T=3; complement x -> 3-x.  Input bytes may be upper
+ * or lower case; any other byte (e.g. N) splits a read into fragments, and no
+ * (k+1)-mer crosses a split.
+ *
+ * Keys: a string s[0..n-1] is the integer sum s[i] * 4^(n-1-i) (first symbol
+ * most significant, so integer order is lexicographic order), stored in nw
+ * little-endian 64-bit words (word 0 least significant); nw = 1, 2 or 4 for
+ * 2(k+1) <= 64, 128 or 256 bits.  Unused high bits are zero.
+ *
+ * SdBG entry codes in W: $=0, A=1, C=2, G=3, T=4, plus 4 when the minus flag
+ * is set (an edge into a target that an earlier entry already enters).
+ * Bit-vectors are arrays of uint32 words, entry i at bit (i % 32) of word
+ * i / 32; bits past the last entry are zero.
+ *
+ * Memory and streams
+ * ------------------
+ * Every call runs on the context's stream, in order.  Outputs are allocated
+ * by the library through the context's allocator (the caller's callbacks, or
+ * a stream-ordered pool of the context's device) and belong to the returned
+ * handle until mh_free_*.  Views return borrowed device pointers, valid while
+ * the handle lives.  Calls that must size their output wait once for a small
+ * device-to-host copy; all other work is asynchronous.
+ *
+ * Errors
+ * ------
+ * Every int-returning call returns MH_OK (0) or a negative MH_E* code; on
+ * error no output handle is produced (*out is set to NULL) and the inputs
+ * are unchanged.  mh_last_error_message(ctx) describes the last failure.
+ * No call aborts the process.  Device-side waits are bounded; a wait that
+ * runs out reports MH_ETIMEOUT instead of hanging.
+ */
+#ifndef MH_H
+#define MH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MH_OK 0
+#define MH_EINVAL (-1)       /* bad argument: k < 2 or k > 127, d < 1, NULL, k mismatch */
+#define MH_ENOMEM (-2)       /* allocation failed or the HBM budget is exceeded */
+#define MH_EOVERFLOW (-3)    /* a count or size does not fit its integer type */
+#define MH_ETIMEOUT (-4)     /* a bounded device wait ran out */
+#define MH_EDEVICE (-5)      /* a CUDA call failed */
+#define MH_EUNSUPPORTED (-6) /* the request is valid but not implemented */
+
+typedef struct mh_ctx mh_ctx;
+typedef struct mh_reads mh_reads;
+typedef struct mh_kmers mh_kmers;
+typedef struct mh_sdbg mh_sdbg;
+
+/* Allocator callbacks.  alloc returns device memory of at least `bytes`
+ * bytes, usable in stream order on `stream`, or NULL on failure; free returns
+ * it.  `user` is mh_config.alloc_user. */
+typedef void* (*mh_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*mh_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+
+typedef struct {
+    int device;            /* CUDA device ordinal */
+    void* stream;          /* cudaStream_t to run on; NULL = a stream the context creates */
+    uint64_t hbm_budget;   /* max bytes the context may hold at once; 0 = no limit */
+    mh_alloc_fn alloc;     /* NULL = the library's stream-ordered pool */
+    mh_free_fn free;       /* must be set iff alloc is set */
+    void* alloc_user;
+    int with_mult;         /* 1: mh_build_sdbg also emits mult[] (edge counts) */
+    int profile;           /* 1: time every kernel launch with CUDA events */
+} mh_config;
+
+/* Create a context on cfg->device.  Returns MH_OK and *out, or an error. */
+int mh_create(const mh_config* cfg, mh_ctx** out);
+void mh_destroy(mh_ctx* ctx);
+
+/* ---------------------------------------------------------------- reads */
+
+/* Pack reads into 2-bit codes, split at bytes outside ACGTacgt.
+ *   ascii      n_bases bytes: all reads back to back (host or device memory)
+ *   offs       n_reads + 1 uint64 offsets into ascii, non-decreasing,
+ *              offs[0] = 0, offs[n_reads] = n_bases (same memory kind as ascii)
+ *   on_device  1 if ascii and offs are device pointers, 0 if host pointers
+ *              (host memory is copied in on the context's stream; pinned
+ *              memory makes that copy asynchronous)
+ * The handle holds the fragments (maximal runs of valid bases, empty reads
+ * contribute none) packed back to back: base j of the packed stream at bits
+ * 31-2(j%16) of word j/16, frag_offs[f]..frag_offs[f+1] the bases of fragment
+ * f, frag_read[f] its read.  Errors: MH_EINVAL (NULL pointer, offs not
+ * monotone), MH_ENOMEM. */
+int mh_pack_reads(mh_ctx* ctx, const uint8_t* ascii, uint64_t n_bases, const uint64_t* offs,
+                  uint64_t n_reads, int on_device, mh_reads** out);
+
+typedef struct {
+    uint64_t n_reads, n_bases;  /* as given */
+    uint64_t n_frags;           /* fragments */
+    uint64_t n_packed;          /* bases in the packed stream (valid bases) */
+    const uint32_t* packed;     /* device, ceil(n_packed/16) words (+ zero padding) */
+    const uint64_t* frag_offs;  /* device, n_frags + 1 */
+    const uint32_t* frag_read;  /* device, n_frags */
+} mh_reads_view;
+int mh_reads_view_get(const mh_reads* r, mh_reads_view* v);
+void mh_free_reads(mh_reads* r);
+
+/* ------------------------------------------------------------ counting */
+
+/* Count every (k+1)-mer of every fragment on both strands (each window adds
+ * one to itself and one to its reverse complement, so a palindromic (k+1)-mer
+ * gains two) and keep those with count >= d: the solid (k+1)-mers, sorted
+ * ascending, closed under reverse complement, with exact uint32 counts.
+ * 2 <= k <= 127, d >= 1.  The handle also keeps the sorted count spectrum
+ * that mh_mercy_kmers needs.  Errors: MH_EINVAL, MH_ENOMEM, MH_EOVERFLOW (a
+ * count above 2^32-1), MH_ETIMEOUT, MH_EDEVICE. */
+int mh_count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers** solid_out);
+
+/* Mercy (k+1)-mers.  Degrees are those of the solid graph: x has no
+ * outdegree if no solid edge starts with x[1..k]; y has no indegree if no
+ * solid edge ends with y[0..k-1].  In each fragment, forward strand, for two
+ * consecutive solid positions p < q with q > p+1, x = edge p without
+ * outdegree and y = edge q without indegree, the edges at p+1..q-1 are mercy
+ * edges.  The result is closed under reverse complement, sorted, disjoint
+ * from the solid set, and carries each edge's count from mh_count_kmers (in
+ * [1, d-1]).  `solid` must come from mh_count_kmers on the same reads.
+ * Errors: MH_EINVAL, MH_ENOMEM, MH_ETIMEOUT, MH_EDEVICE. */
+int mh_mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_kmers** mercy_out);
+
+typedef struct {
+    int k, nw;                /* (k+1)-mers, nw words per key */
+    uint64_t n;               /* keys */
+    const uint64_t* keys;     /* device, n * nw words, ascending */
+    const uint32_t* counts;   /* device, n */
+    uint64_t n_kmers;         /* |K|: all (k+1)-mers on both strands (counting handles) */
+    uint64_t n_distinct;      /* distinct (k+1)-mers in K (counting handles) */
+} mh_kmers_view;
+int mh_kmers_view_get(const mh_kmers* s, mh_kmers_view* v);
+void mh_free_kmers(mh_kmers* s);
+
+/* ---------------------------------------------------------------- SdBG */
+
+/* Build the BOSS arrays of the edge set E = solid + mercy (mercy may be
+ * NULL).  Entries are E plus padding, in colex order: node symbols k-1 down
+ * to 0, then the label, with $ below every base.
+ *   * every zero-indegree node v gets ONE dummy entry: node $ v[0..k-2],
+ *     label v[k-1]; v is stored in aux (nw words each, k symbols), in the
+ *     order of the dummy entries (t of them, so aux is the 2kt-bit store);
+ *   * every node with no outgoing edge gets one entry labelled $ (u of them);
+ *   * last[i] = 1 iff entry i is its node's final entry; dummy[i] marks the
+ *     dummy entries; valid[i] = 1 for every entry;
+ *   * F[c] = number of entries whose node ends with a symbol below c, for c
+ *     in $ A C G T, and F[5] = m.
+ * Errors: MH_EINVAL (k mismatch), MH_ENOMEM, MH_ETIMEOUT, MH_EDEVICE. */
+int mh_build_sdbg(mh_ctx* ctx, const mh_kmers* solid, const mh_kmers* mercy, mh_sdbg** out);
+
+typedef struct {
+    int k, nw;
+    uint64_t m;               /* entries */
+    uint64_t t;               /* dummy entries = zero-indegree nodes */
+    uint64_t u;               /* $ entries = zero-outdegree nodes */
+    uint64_t n_nodes;         /* popcount(last) */
+    uint64_t F[6];            /* host copy */
+    const uint8_t* W;         /* device, m */
+    const uint32_t* last;     /* device, ceil(m/32) words */
+    const uint32_t* valid;    /* device, ceil(m/32) words */
+    const uint32_t* dummy;    /* device, ceil(m/32) words */
+    const uint64_t* aux;      /* device, t * nw words */
+    const uint32_t* mult;     /* device, m, or NULL unless with_mult */
+} mh_sdbg_view;
+int mh_sdbg_view_get(const mh_sdbg* g, mh_sdbg_view* v);
+void mh_free_sdbg(mh_sdbg* g);
+
+/* ------------------------------------------------------------ utilities */
+
+const char* mh_strerror(int code);
+const char* mh_last_error_message(const mh_ctx* ctx);
+
+/* The context's stream (a cudaStream_t). */
+void* mh_stream(const mh_ctx* ctx);
+
+/* Bytes the context holds now, and the most it has held. */
+void mh_memory(const mh_ctx* ctx, uint64_t* in_use, uint64_t* peak);
+
+/* Per-kernel launch statistics gathered while cfg.profile = 1.  Waits for the
+ * stream.  For index i in [0, mh_profile_count()), writes the kernel's name
+ * (NUL-terminated, at most name_cap bytes), its launch count and the sum of
+ * its CUDA-event durations in milliseconds.  mh_profile_reset clears them. */
+int mh_profile_count(mh_ctx* ctx);
+int mh_profile_get(mh_ctx* ctx, int i, char* name, int name_cap, uint64_t* launches, double* total_ms);
+void mh_profile_reset(mh_ctx* ctx);
+void mh_set_profile(mh_ctx* ctx, int on);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MH_H */

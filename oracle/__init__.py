@@ -77,6 +77,8 @@ def _load():
             lib.orc_count_queries.argtypes = [u8p, u64p, ctypes.c_uint64, ctypes.c_int, u64p,
                                               ctypes.c_uint64, u64p, ctypes.c_int]
             lib.orc_count_queries.restype = ctypes.c_int
+            lib.orc_fragments.argtypes = [u8p, u64p, ctypes.c_uint64, ctypes.c_char_p, u64p, u32p]
+            lib.orc_fragments.restype = ctypes.c_uint64
             _lib = lib
     return _lib
 
@@ -94,6 +96,23 @@ def _arr(ptr, n, dtype):
 
 def _p(a, ct):
     return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def fragments(ascii, offs):
+    """(bases, frag_offs, frag_read): the fragments of every read (maximal
+    ACGT runs, upper-cased) back to back as bytes, their offsets and reads."""
+    lib = _load()
+    ascii = np.ascontiguousarray(ascii, dtype=np.uint8)
+    offs = np.ascontiguousarray(offs, dtype=np.uint64)
+    n_reads = len(offs) - 1
+    buf = ctypes.create_string_buffer(max(1, len(ascii)))
+    fo = np.zeros(len(ascii) + 2, dtype=np.uint64)
+    fr = np.zeros(len(ascii) + 1, dtype=np.uint32)
+    a = ascii if len(ascii) else np.zeros(1, dtype=np.uint8)
+    nf = lib.orc_fragments(_p(a, ctypes.c_uint8), _p(offs, ctypes.c_uint64), n_reads, buf,
+                           _p(fo, ctypes.c_uint64), _p(fr, ctypes.c_uint32))
+    total = int(fo[nf])
+    return buf.raw[:total], fo[:nf + 1].copy(), fr[:nf].copy()
 
 
 def count(ascii, offs, k: int, d: int = 2, mercy: bool = True) -> dict:

@@ -225,6 +225,25 @@ static void put_keys(const std::vector<std::string>& v, int nw, uint64_t** keys)
     for (size_t i = 0; i < v.size(); i++) encode(v[i], nw, *keys + i * nw);
 }
 
+// C1 alone: the fragments (maximal ACGT runs, upper-cased) of every read,
+// concatenated into `bases` (capacity n_bases), with n_frags + 1 offsets into
+// it and the read of each fragment.  Returns the number of fragments.
+uint64_t orc_fragments(const uint8_t* ascii, const uint64_t* offs, uint64_t n_reads, char* bases,
+                       uint64_t* frag_offs, uint32_t* frag_read) {
+    uint64_t nf = 0, pos = 0;
+    frag_offs[0] = 0;
+    for (uint64_t r = 0; r < n_reads; r++) {
+        std::vector<std::string> fr = fragments(ascii, offs + r, 1);
+        for (const std::string& s : fr) {
+            std::memcpy(bases + pos, s.data(), s.size());
+            pos += s.size();
+            frag_read[nf] = (uint32_t)r;
+            frag_offs[++nf] = pos;
+        }
+    }
+    return nf;
+}
+
 // Counting (C1-C3) and, if do_mercy, mercy (M1-M4).
 orc_kmer_result* orc_count(const uint8_t* ascii, const uint64_t* offs, uint64_t n_reads, int k,
                            int d, int do_mercy) {

@@ -1,0 +1,404 @@
+// Internal declarations of the SdBG construction library (sm_103a).
+//
+// Keys are multiword integers (Key<NW>, NW = 1, 2, 4 little-endian 64-bit
+// words) holding 2-bit symbols, first symbol most significant; see mh.h for
+// the layout.  Every kernel runs on the context's stream; every device-side
+// wait is bounded and reports through the context's status word.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+#include "mh.h"
+
+namespace mh {
+
+// ------------------------------------------------------------ status bits
+// Set by kernels with atomicOr on ctx->d_status, checked by the host after
+// the call's synchronising copy.
+constexpr uint32_t ST_SPIN_TIMEOUT = 1u;  // a bounded look-back wait gave up
+constexpr uint32_t ST_OVERFLOW = 2u;      // a count did not fit 32 bits
+constexpr uint32_t ST_TABLE_FULL = 4u;    // a hash probe sequence ran out
+constexpr uint32_t ST_BAD_INPUT = 8u;     // read offsets not monotone or out of range
+
+struct Error {
+    int code;
+    std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string& msg);
+void cuda_check(cudaError_t e, const char* what);
+#define MH_CUDA(call) ::mh::cuda_check((call), #call)
+
+}  // namespace mh
+
+struct KernelStat {
+    uint64_t launches = 0;
+    double total_ms = 0.0;
+};
+
+struct mh_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    mh_alloc_fn alloc = nullptr;
+    mh_free_fn free_fn = nullptr;
+    void* alloc_user = nullptr;
+    cudaMemPool_t pool = nullptr;
+    uint64_t budget = 0, in_use = 0, peak = 0;
+    std::unordered_map<void*, size_t> sizes;
+    int with_mult = 0;
+    int num_sms = 0;
+    uint32_t* d_status = nullptr;  // device status word (ST_* bits)
+    uint64_t* h_pinned = nullptr;  // small pinned buffer for read-backs (64 words)
+    // profiling
+    int profile = 0;
+    std::vector<cudaEvent_t> ev_free;
+    struct Pending {
+        int name;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<std::string> names;
+    std::unordered_map<std::string, int> name_id;
+    std::vector<KernelStat> stats;
+    std::string last_error;
+};
+
+struct mh_reads {
+    uint64_t n_reads = 0, n_bases = 0, n_frags = 0, n_packed = 0;
+    uint32_t* packed = nullptr;     // ceil(n_packed/16) + kPackPad words
+    uint64_t* frag_offs = nullptr;  // n_frags + 1
+    uint32_t* frag_read = nullptr;  // n_frags
+    mh_ctx* ctx = nullptr;
+};
+
+struct mh_kmers {
+    int k = 0, nw = 1, d = 0;
+    uint64_t n = 0;
+    uint64_t* keys = nullptr;   // n * nw
+    uint32_t* counts = nullptr; // n
+    // counting handles: the sorted canonical spectrum (min(x, rc x) of every
+    // window, with repeats) kept for the mercy counts
+    uint64_t* spectrum = nullptr;
+    uint64_t n_spectrum = 0;
+    uint64_t n_kmers = 0, n_distinct = 0;
+    mh_ctx* ctx = nullptr;
+};
+
+struct mh_sdbg {
+    int k = 0, nw = 1;
+    uint64_t m = 0, t = 0, u = 0, n_nodes = 0;
+    uint64_t F[6] = {0, 0, 0, 0, 0, 0};
+    uint8_t* W = nullptr;
+    uint32_t* last = nullptr;
+    uint32_t* valid = nullptr;
+    uint32_t* dummy = nullptr;
+    uint64_t* aux = nullptr;
+    uint32_t* mult = nullptr;
+    mh_ctx* ctx = nullptr;
+};
+
+namespace mh {
+
+constexpr int kPackPad = 12;  // zero words after the packed stream (window loads read ahead)
+
+// ----------------------------------------------------------- allocation
+void* ctx_alloc(mh_ctx* ctx, size_t bytes);
+void ctx_free(mh_ctx* ctx, void* p);
+
+// Owning device buffer; frees through the context unless released.
+template <class T>
+struct Buf {
+    mh_ctx* ctx = nullptr;
+    T* p = nullptr;
+    size_t n = 0;
+    Buf() = default;
+    Buf(mh_ctx* c, size_t count) : ctx(c), n(count) {
+        p = static_cast<T*>(ctx_alloc(c, (count ? count : 1) * sizeof(T)));
+    }
+    Buf(const Buf&) = delete;
+    Buf& operator=(const Buf&) = delete;
+    Buf(Buf&& o) noexcept : ctx(o.ctx), p(o.p), n(o.n) { o.p = nullptr; }
+    Buf& operator=(Buf&& o) noexcept {
+        reset();
+        ctx = o.ctx; p = o.p; n = o.n; o.p = nullptr;
+        return *this;
+    }
+    ~Buf() { reset(); }
+    void reset() {
+        if (p) ctx_free(ctx, p);
+        p = nullptr;
+    }
+    T* release() {
+        T* q = p;
+        p = nullptr;
+        return q;
+    }
+    void zero() { MH_CUDA(cudaMemsetAsync(p, 0, (n ? n : 1) * sizeof(T), ctx->stream)); }
+};
+
+// ------------------------------------------------------ launch profiling
+struct Prof {
+    mh_ctx* ctx;
+    int id = -1;
+    cudaEvent_t a = nullptr, b = nullptr;
+    Prof(mh_ctx* c, const char* name);
+    ~Prof();
+};
+
+// Launch a kernel on the context stream, timed when profiling is on.
+#define MH_LAUNCH(ctx, name, grid, block, smem, kernel, ...)                          \
+    do {                                                                               \
+        ::mh::Prof _mh_prof((ctx), (name));                                            \
+        kernel<<<(grid), (block), (smem), (ctx)->stream>>>(__VA_ARGS__);               \
+        ::mh::cuda_check(cudaGetLastError(), (name));                                  \
+    } while (0)
+
+// Wait for the stream, then raise the first status bit the kernels set.
+void sync_and_check(mh_ctx* ctx);
+// Copy `count` uint64 from device to host through the pinned buffer (waits).
+void read_u64(mh_ctx* ctx, const uint64_t* d, uint64_t* h, int count);
+
+__host__ __device__ inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+inline int words_for(int k) { return 2 * (k + 1) <= 64 ? 1 : (2 * (k + 1) <= 128 ? 2 : 4); }
+int grid_for(mh_ctx* ctx, uint64_t work_items, int per_block, int blocks_per_sm = 8);
+
+// ------------------------------------------------------------ key helpers
+template <int NW>
+struct Key {
+    uint64_t w[NW];
+};
+
+template <int NW>
+__host__ __device__ __forceinline__ bool key_less(const Key<NW>& a, const Key<NW>& b) {
+#pragma unroll
+    for (int i = NW - 1; i >= 0; i--)
+        if (a.w[i] != b.w[i]) return a.w[i] < b.w[i];
+    return false;
+}
+
+template <int NW>
+__host__ __device__ __forceinline__ bool key_eq(const Key<NW>& a, const Key<NW>& b) {
+    bool e = true;
+#pragma unroll
+    for (int i = 0; i < NW; i++) e &= a.w[i] == b.w[i];
+    return e;
+}
+
+template <int NW>
+__device__ __forceinline__ Key<NW> key_zero() {
+    Key<NW> r;
+#pragma unroll
+    for (int i = 0; i < NW; i++) r.w[i] = 0;
+    return r;
+}
+
+// Word j of a key (0 past the top), without a run-time array index (which
+// would move the key to local memory).
+template <int NW>
+__device__ __forceinline__ uint64_t key_word(const Key<NW>& a, int j) {
+    uint64_t v = 0;
+#pragma unroll
+    for (int m = 0; m < NW; m++) v = (j == m) ? a.w[m] : v;
+    return v;
+}
+
+// Bits [shift, shift+8) of the key, 0 <= shift < 64*NW (bits past the top read 0).
+template <int NW>
+__device__ __forceinline__ uint32_t key_digit(const Key<NW>& a, int shift) {
+    if constexpr (NW == 1) {
+        return (uint32_t)(a.w[0] >> shift) & 0xFFu;
+    } else {
+        int wi = shift >> 6, sb = shift & 63;
+        uint64_t v = key_word<NW>(a, wi) >> sb;
+        if (sb > 56) v |= key_word<NW>(a, wi + 1) << (64 - sb);
+        return (uint32_t)(v & 0xFF);
+    }
+}
+
+// a >> s for 0 <= s < 64*NW
+template <int NW>
+__device__ __forceinline__ Key<NW> key_shr(const Key<NW>& a, int s) {
+    Key<NW> r;
+    if constexpr (NW == 1) {
+        r.w[0] = a.w[0] >> s;
+    } else {
+        int ws = s >> 6, bs = s & 63;
+#pragma unroll
+        for (int i = 0; i < NW; i++) {
+            uint64_t lo = key_word<NW>(a, i + ws), hi = key_word<NW>(a, i + ws + 1);
+            r.w[i] = bs ? ((lo >> bs) | (hi << (64 - bs))) : lo;
+        }
+    }
+    return r;
+}
+
+// a << s for 0 <= s < 64*NW (bits shifted past the top are dropped)
+template <int NW>
+__device__ __forceinline__ Key<NW> key_shl(const Key<NW>& a, int s) {
+    Key<NW> r;
+    if constexpr (NW == 1) {
+        r.w[0] = a.w[0] << s;
+    } else {
+        int ws = s >> 6, bs = s & 63;
+#pragma unroll
+        for (int i = 0; i < NW; i++) {
+            uint64_t hi = key_word<NW>(a, i - ws), lo = key_word<NW>(a, i - ws - 1);
+            r.w[i] = bs ? ((hi << bs) | (lo >> (64 - bs))) : hi;
+        }
+    }
+    return r;
+}
+
+// Keep the low `bits` bits (0 <= bits <= 64*NW).
+template <int NW>
+__device__ __forceinline__ Key<NW> key_low(const Key<NW>& a, int bits) {
+    Key<NW> r;
+#pragma unroll
+    for (int i = 0; i < NW; i++) {
+        int lo = 64 * i;
+        r.w[i] = bits <= lo ? 0 : (bits >= lo + 64 ? a.w[i] : (a.w[i] & ((1ull << (bits - lo)) - 1)));
+    }
+    return r;
+}
+
+template <int NW>
+__device__ __forceinline__ Key<NW> key_or_low(Key<NW> a, uint64_t v) {
+    a.w[0] |= v;
+    return a;
+}
+
+// Reverse the order of the 2-bit symbols of a 64-bit word.
+__device__ __forceinline__ uint64_t rev2_u64(uint64_t x) {
+    uint64_t y = __brevll(x);
+    return ((y >> 1) & 0x5555555555555555ull) | ((y & 0x5555555555555555ull) << 1);
+}
+
+// Reverse the order of the low n symbols (n >= 1) of a key.
+template <int NW>
+__device__ __forceinline__ Key<NW> key_rev(const Key<NW>& a, int n) {
+    Key<NW> r;
+#pragma unroll
+    for (int i = 0; i < NW; i++) r.w[i] = rev2_u64(a.w[NW - 1 - i]);
+    return key_shr<NW>(r, 64 * NW - 2 * n);
+}
+
+// Reverse complement of a string of n symbols (n >= 1).
+template <int NW>
+__device__ __forceinline__ Key<NW> key_rc(const Key<NW>& a, int n) {
+    Key<NW> c;
+#pragma unroll
+    for (int i = 0; i < NW; i++) c.w[i] = ~a.w[i];
+    return key_rev<NW>(key_low<NW>(c, 2 * n), n);
+}
+
+// Symbol i (0 = first) of a string of n symbols.
+template <int NW>
+__device__ __forceinline__ uint32_t key_sym(const Key<NW>& a, int n, int i) {
+    int bit = 2 * (n - 1 - i);
+    return (uint32_t)(key_word<NW>(a, bit >> 6) >> (bit & 63)) & 3u;
+}
+
+template <int NW>
+__device__ __forceinline__ Key<NW> load_key(const uint64_t* p, uint64_t i) {
+    Key<NW> r;
+    if constexpr (NW == 1) {
+        r.w[0] = p[i];
+    } else if constexpr (NW == 2) {
+        ulonglong2 v = reinterpret_cast<const ulonglong2*>(p)[i];
+        r.w[0] = v.x; r.w[1] = v.y;
+    } else {
+        const ulonglong2* q = reinterpret_cast<const ulonglong2*>(p) + 2 * i;
+        ulonglong2 v0 = q[0], v1 = q[1];
+        r.w[0] = v0.x; r.w[1] = v0.y; r.w[2] = v1.x; r.w[3] = v1.y;
+    }
+    return r;
+}
+
+template <int NW>
+__device__ __forceinline__ void store_key(uint64_t* p, uint64_t i, const Key<NW>& k) {
+    if constexpr (NW == 1) {
+        p[i] = k.w[0];
+    } else if constexpr (NW == 2) {
+        reinterpret_cast<ulonglong2*>(p)[i] = make_ulonglong2(k.w[0], k.w[1]);
+    } else {
+        ulonglong2* q = reinterpret_cast<ulonglong2*>(p) + 2 * i;
+        q[0] = make_ulonglong2(k.w[0], k.w[1]);
+        q[1] = make_ulonglong2(k.w[2], k.w[3]);
+    }
+}
+
+// The n symbols starting at base p of the packed stream (base j at bits
+// 31-2(j%16) of word j/16), as a key.  Reads up to 2*NW+1 words from p/16.
+template <int NW>
+__device__ __forceinline__ Key<NW> load_window(const uint32_t* __restrict__ packed, uint64_t p, int n) {
+    const uint32_t* w = packed + (p >> 4);
+    int o = 2 * (int)(p & 15);
+    uint32_t s32[2 * NW];
+    uint32_t cur = w[0];
+#pragma unroll
+    for (int t = 0; t < 2 * NW; t++) {
+        uint32_t nxt = w[t + 1];
+        s32[t] = o ? ((cur << o) | (nxt >> (32 - o))) : cur;
+        cur = nxt;
+    }
+    Key<NW> r;
+#pragma unroll
+    for (int j = 0; j < NW; j++) r.w[NW - 1 - j] = ((uint64_t)s32[2 * j] << 32) | s32[2 * j + 1];
+    return key_shr<NW>(r, 64 * NW - 2 * n);
+}
+
+// ------------------------------------------------------ bounded waits
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ----------------------------------------------------------- hashing
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+template <int NW>
+__device__ __forceinline__ uint64_t key_hash(const Key<NW>& a) {
+    uint64_t h = 0x9E3779B97F4A7C15ull;
+#pragma unroll
+    for (int i = 0; i < NW; i++) h = mix64(h ^ a.w[i]);
+    return h;
+}
+
+// ------------------------------------------------------------- sorting
+// LSD radix sort (one digit histogram pass, then one onesweep pass per
+// 8-bit digit of bits [bit_lo, bit_hi)).  keys/alt (and vals/valt when
+// vals != nullptr) are n-element buffers; returns true if the sorted data
+// ended in alt/valt, false if in keys/vals.
+template <int NW>
+bool radix_sort(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt, uint64_t n,
+                int bit_lo, int bit_hi);
+
+// ---------------------------------------------------------------- scans
+// out[i] = sum of in[0..i-1] for i in [0, n]; out has n+1 entries.
+void exclusive_scan_u64(mh_ctx* ctx, const uint64_t* in, uint64_t* out, uint64_t n);
+void exclusive_scan_u32(mh_ctx* ctx, const uint32_t* in, uint64_t* out, uint64_t n);
+
+// ------------------------------------------------- counting stages
+// Sorted canonical spectrum -> solid (k+1)-mers, both strands, sorted.
+// Defined in mh_count.cu, used by mercy too (d = 1, counts looked up).
+template <int NW>
+void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, Buf<uint64_t>& out_keys,
+                 Buf<uint32_t>& out_cnt, uint64_t* n_out, uint64_t* n_canon_runs, uint64_t* n_palin_runs,
+                 const uint64_t* spectrum, uint64_t n_spectrum);
+
+}  // namespace mh
