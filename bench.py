@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Benchmark of the SdBG construction path on synthetic reads.
+
+One step = the whole path on one read set: mh_pack_reads (from reads already
+in HBM), mh_count_kmers, mh_mercy_kmers, mh_build_sdbg.  The default
+workload is the simulated metagenome: 100 random genomes (lognormal lengths,
+median 2 Mbp; lognormal abundances), 10 M read pairs of 2 x 150 bp (3.0 Gbp),
+substitution rate rising to 1% at the 3' end, k = 31, d = 2.
+
+value       (k+1)-mers counted per second: |K| (every (k+1)-mer on both
+            strands) of all ranks' read sets / max-over-ranks step time
+e2e         the same through the C ABI from pinned host buffers, with the
+            read upload and the download of the SdBG arrays in the timed region
+roofline    the radix scatter pass (the dominant kernel): algorithmic bytes
+            (2 x key bytes per key, + 2 x 4 for a payload) / its CUDA-event
+            time, against the measured HBM copy bandwidth
+cpu_baseline  the CPU oracle, single thread, on the first 24,000 reads
+
+``--impl reference`` times the CPU oracle alone (rank 0) on that sample.
+Multi-GPU (torchrun): every rank builds its own independent read set (seed +
+rank), so per-GPU work is fixed (weak scaling); there is no collective on the
+data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "(k+1)-mers sorted+counted/s and SdBG edges built/s, % of HBM peak; served p50/p99"
+UNIT = "(k+1)-mers/s"
+CPU_SAMPLE_READS = 24_000
+
+WORKLOADS = {
+    "metagenome": {
+        "name": "simulated metagenome: 100 genomes (lognormal lengths, median 2 Mbp, sigma 0.5; "
+                "lognormal abundances, sigma 1.5), 10M pairs 2x150 bp, 3' error ramp to 1% (mean 0.5%), "
+                "k=31, d=2, mercy on",
+        "k": 31, "d": 2, "seed": 2,
+        "gen": lambda seed: __import__("synth").metagenome_reads(seed=seed),
+        "sample": lambda seed, n: __import__("synth").metagenome_reads(seed=seed, n_pairs=n // 2),
+    },
+    "plain": {
+        "name": "plain single job: uniform 50 kbp genome, 10,000 x 100 bp single-end reads, 1% errors, "
+                "k=21, d=2, mercy on",
+        "k": 21, "d": 2, "seed": 1,
+        "gen": lambda seed: __import__("synth").uniform_genome_reads(seed=seed),
+        "sample": lambda seed, n: __import__("synth").uniform_genome_reads(seed=seed, n_reads=min(n, 10_000)),
+    },
+}
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="metagenome", choices=sorted(WORKLOADS))
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _traffic_record():
+    """ncu DRAM bytes per key of the scatter pass, if recorded for the current
+    kernel source."""
+    path = os.path.join(ROOT, "profiles", "radix_onesweep_traffic.json")
+    src = os.path.join(ROOT, "paper_1409_7208_gb300", "csrc", "mh_sort.cu")
+    try:
+        rec = json.load(open(path))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        return rec if rec.get("mh_sort_cu_sha256") == sha else None
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank):
+        self.proc = None
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        self.index = vis.split(",")[local_rank] if vis else str(local_rank)
+        self.tmp = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.index, "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.split(",") for r in self.tmp.read().strip().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for name, v in zip(names, r[5:9]):
+                    if v.strip() == "Active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_run(ascii, offs, k, d):
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.count(ascii, offs, k, d, mercy=True)
+    oracle.build_sdbg(k, r["solid_keys"], r["solid_cnt"], r["mercy_keys"], r["mercy_cnt"])
+    return r["n_kmers"], time.perf_counter() - t0
+
+
+def run_reference(args, wl, rank, world):
+    """The CPU oracle as it stands, one thread, on the bounded sample."""
+    if rank != 0:
+        return
+    ascii, offs = wl["sample"](wl["seed"], CPU_SAMPLE_READS)
+    for _ in range(args.warmup):
+        cpu_oracle_run(ascii, offs, wl["k"], wl["d"])
+    total_n, total_t = 0, 0.0
+    for _ in range(args.steps):
+        n, t = cpu_oracle_run(ascii, offs, wl["k"], wl["d"])
+        total_n += n
+        total_t += t
+    v = total_n / total_t
+    sample = "first %d reads of the workload (%d (k+1)-mers on both strands)" % (len(offs) - 1, n)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": {"workload": wl["name"], "k": wl["k"], "d": wl["d"],
+                                            "sample_reads": len(offs) - 1},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    wl = WORKLOADS[args.workload]
+    rank, world, local = _dist()
+    if args.impl == "reference":
+        return run_reference(args, wl, rank, world)
+
+    import numpy as np
+    import torch
+
+    import paper_1409_7208_gb300 as mh
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    k, d = wl["k"], wl["d"]
+    ascii, offs = wl["gen"](wl["seed"] + 1000 * rank)
+    n_bases = len(ascii)
+    stream = torch.cuda.current_stream()
+    ctx = mh.Context(device=local, stream=stream)
+    d_ascii = torch.from_numpy(ascii).cuda()
+    d_offs = torch.from_numpy(offs.view(np.int64)).cuda()
+    torch.cuda.synchronize()
+
+    info = {}
+
+    def step(ascii_in, offs_in, phases=None, download=None):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if phases is not None else None
+        if ev:
+            ev[0].record(stream)
+        reads = mh.mh_pack_reads(ctx, ascii_in, offs_in)
+        if ev:
+            ev[1].record(stream)
+        solid = mh.mh_count_kmers(ctx, reads, k, d)
+        if ev:
+            ev[2].record(stream)
+        mercy = mh.mh_mercy_kmers(ctx, reads, solid)
+        if ev:
+            ev[3].record(stream)
+        g = mh.mh_build_sdbg(ctx, solid, mercy)
+        if ev:
+            ev[4].record(stream)
+        sv, gv = solid.view(), g.view()
+        info.update(n_kmers=sv.n_kmers, n_distinct=sv.n_distinct, solid=sv.n, mercy=mercy.view().n,
+                    m=gv.m, t=gv.t, u=gv.u)
+        if download is not None:
+            download(g)
+        if ev:
+            phases.append(ev)
+        del g, mercy, solid, reads
+
+    for _ in range(args.warmup):
+        step(d_ascii, d_offs)
+    torch.cuda.synchronize()
+    barrier()
+
+    clocks = Clocks(local)
+    clocks.start()
+    ctx.profile_reset()
+    ctx.set_profile(True)
+    phases = []
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step(d_ascii, d_offs, phases)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ctx.set_profile(False)
+    clk = clocks.stop()
+    ms = t_start.elapsed_time(t_end)
+    prof = ctx.profile()
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    n_kmers = info["n_kmers"]
+    value = n_kmers * world * args.steps / (ms / 1e3)
+    phase_ms = {name: sum(p[i].elapsed_time(p[i + 1]) for p in phases) / len(phases)
+                for i, name in enumerate(["pack", "count", "mercy", "build"])}
+
+    # end to end through host buffers: upload of the reads and download of the SdBG
+    pin_ascii = torch.from_numpy(ascii).pin_memory()
+    pin_offs = torch.from_numpy(offs.view(np.int64)).pin_memory()
+    d2h = {"bytes": 0}
+    host_bufs = {}
+
+    def download(g):
+        t = g.tensors()
+        nbytes = 0
+        for key in ("W", "last", "valid", "dummy", "aux"):
+            src = t[key]
+            buf = host_bufs.get(key)
+            if buf is None or buf.numel() < src.numel():
+                buf = torch.empty(max(1, src.numel()), dtype=src.dtype, pin_memory=True)
+                host_bufs[key] = buf
+            if src.numel():
+                buf[: src.numel()].view(src.shape).copy_(src, non_blocking=True)
+            nbytes += src.numel() * src.element_size()
+        stream.synchronize()
+        d2h["bytes"] = nbytes + 48  # + F, returned by value
+
+    step(pin_ascii, pin_offs, None, download)  # warm the host path
+    torch.cuda.synchronize()
+    barrier()
+    e0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        step(pin_ascii, pin_offs, None, download)
+    torch.cuda.synchronize()
+    e_s = time.perf_counter() - e0
+    if dist is not None:
+        t = torch.tensor([e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_s = float(t.item())
+    e2e = {"value": n_kmers * world * args.e2e_steps / e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(n_bases + offs.nbytes), "d2h_bytes_per_step": int(d2h["bytes"])}
+
+    # roofline of the dominant kernel (radix scatter pass)
+    peak, peak_kind = _peak_hbm()
+    launches, o_ms, o_bytes = prof.get("radix_onesweep", (0, 0.0, 0))
+    achieved = o_bytes / (o_ms / 1e3) / 1e9 if o_ms > 0 else 0.0
+    rec = _traffic_record()
+    traffic = None
+    if rec and launches:
+        keys_per_launch = o_bytes / launches / 16.0
+        traffic = rec["dram_bytes_per_key"] * keys_per_launch
+    roofline = {"bound": "hbm", "kernel": "radix_onesweep", "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "algorithmic_bytes_per_launch": (o_bytes / launches) if launches else 0,
+                "avg_launch_ms": (o_ms / launches) if launches else 0, "launches": launches}
+    kernels = {name: {"launches": la, "ms_per_step": t / args.steps,
+                      "GB_per_s": (b / (t / 1e3) / 1e9) if (b and t) else None}
+               for name, (la, t, b) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    total_ms = sum(t for (_, t, _) in prof.values())
+    for name in kernels:
+        kernels[name]["share"] = prof[name][1] / total_ms if total_ms else 0
+    gpu_launches = sum(la for (la, _, _) in prof.values())
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sa, so = wl["sample"](wl["seed"], CPU_SAMPLE_READS)
+        n_s, t_s = cpu_oracle_run(sa, so, k, d)
+        cpu = {"value": n_s / t_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "first %d reads of the workload (%d (k+1)-mers on both strands), %.1f s"
+                         % (len(so) - 1, n_s, t_s)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": wl["name"], "reads": len(offs) - 1, "bases": n_bases, "k": k, "d": d,
+                       "per_rank": "independent read set per rank (seed + 1000 * rank)",
+                       "l2": "inputs larger than L2 (%.1f GB of reads, %.1f GB of keys per step)"
+                             % (n_bases / 1e9, info["n_kmers"] * 4 / 1e9)},
+            "sdbg_edges_per_s": info["m"] * world * args.steps / (ms / 1e3),
+            "phases_ms": phase_ms,
+            "sizes": {key: int(v) for key, v in info.items()},
+            "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": gpu_launches, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -202,12 +202,17 @@ void* mh_stream(const mh_ctx* ctx);
 /* Bytes the context holds now, and the most it has held. */
 void mh_memory(const mh_ctx* ctx, uint64_t* in_use, uint64_t* peak);
 
-/* Per-kernel launch statistics gathered while cfg.profile = 1.  Waits for the
- * stream.  For index i in [0, mh_profile_count()), writes the kernel's name
- * (NUL-terminated, at most name_cap bytes), its launch count and the sum of
- * its CUDA-event durations in milliseconds.  mh_profile_reset clears them. */
+/* Per-kernel launch statistics gathered while cfg.profile = 1 (or after
+ * mh_set_profile(ctx, 1)).  Waits for the stream.  For index i in
+ * [0, mh_profile_count()), writes the kernel's name (NUL-terminated, at most
+ * name_cap bytes), its launch count, the sum of its CUDA-event durations in
+ * milliseconds (events recorded on the context stream around each launch)
+ * and the sum of its algorithmic bytes (the reads and writes the step must
+ * do, e.g. 2 x key bytes per key for a radix pass; 0 where not accounted).
+ * mh_profile_reset clears them.  Any output pointer may be NULL. */
 int mh_profile_count(mh_ctx* ctx);
-int mh_profile_get(mh_ctx* ctx, int i, char* name, int name_cap, uint64_t* launches, double* total_ms);
+int mh_profile_get(mh_ctx* ctx, int i, char* name, int name_cap, uint64_t* launches, double* total_ms,
+                   uint64_t* bytes);
 void mh_profile_reset(mh_ctx* ctx);
 void mh_set_profile(mh_ctx* ctx, int on);
 

@@ -106,7 +106,7 @@ def load_library(path: str = LIB_PATH):
     lib.mh_memory.argtypes = [P, ctypes.POINTER(u64), ctypes.POINTER(u64)]
     lib.mh_profile_count.argtypes = [P]
     lib.mh_profile_get.argtypes = [P, ctypes.c_int, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(u64),
-                                   ctypes.POINTER(ctypes.c_double)]
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64)]
     lib.mh_profile_reset.argtypes = [P]
     lib.mh_set_profile.argtypes = [P, ctypes.c_int]
     _lib = lib
@@ -205,14 +205,16 @@ class Context:
         self._lib.mh_set_profile(self._h, 1 if on else 0)
 
     def profile(self) -> dict:
-        """{kernel name: (launches, total ms)} gathered while profiling is on."""
+        """{kernel name: (launches, total ms, algorithmic bytes)} gathered
+        while profiling is on."""
         n = self._lib.mh_profile_count(self._h)
         out = {}
         buf = ctypes.create_string_buffer(128)
         for i in range(n):
-            la, ms = ctypes.c_uint64(), ctypes.c_double()
-            self._check(self._lib.mh_profile_get(self._h, i, buf, 128, ctypes.byref(la), ctypes.byref(ms)))
-            out[buf.value.decode()] = (la.value, ms.value)
+            la, ms, by = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_uint64()
+            self._check(self._lib.mh_profile_get(self._h, i, buf, 128, ctypes.byref(la), ctypes.byref(ms),
+                                                 ctypes.byref(by)))
+            out[buf.value.decode()] = (la.value, ms.value, by.value)
         return out
 
     def profile_reset(self):

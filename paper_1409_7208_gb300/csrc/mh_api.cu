@@ -93,6 +93,7 @@ static void drain_events(mh_ctx* ctx, bool wait) {
         if (e == cudaSuccess) {
             ctx->stats[p.name].launches++;
             ctx->stats[p.name].total_ms += ms;
+            ctx->stats[p.name].bytes += p.bytes;
         } else {
             cudaGetLastError();
         }
@@ -102,7 +103,7 @@ static void drain_events(mh_ctx* ctx, bool wait) {
     ctx->pending.resize(keep);
 }
 
-Prof::Prof(mh_ctx* c, const char* name) : ctx(c) {
+Prof::Prof(mh_ctx* c, const char* name, uint64_t algo_bytes) : ctx(c), bytes(algo_bytes) {
     if (!ctx->profile) return;
     auto it = ctx->name_id.find(name);
     if (it == ctx->name_id.end()) {
@@ -122,7 +123,7 @@ Prof::Prof(mh_ctx* c, const char* name) : ctx(c) {
 Prof::~Prof() {
     if (id < 0) return;
     cudaEventRecord(b, ctx->stream);
-    ctx->pending.push_back({id, a, b});
+    ctx->pending.push_back({id, a, b, bytes});
 }
 
 void sync_and_check(mh_ctx* ctx) {
@@ -242,9 +243,8 @@ int mh_pack_reads(mh_ctx* ctx, const uint8_t* ascii, uint64_t n_bases, const uin
         if (on_device) {
             pack_reads(ctx, ascii, n_bases, offs, n_reads, r.get());
         } else {
+            // monotonicity is checked on the device with the other offset checks
             if (offs[0] != 0 || offs[n_reads] != n_bases) fail(MH_EINVAL, "offs must run from 0 to n_bases");
-            for (uint64_t i = 0; i < n_reads; i++)
-                if (offs[i + 1] < offs[i]) fail(MH_EINVAL, "offs is not non-decreasing");
             Buf<uint8_t> da(ctx, n_bases + 16);
             Buf<uint64_t> doff(ctx, n_reads + 1);
             if (n_bases)
@@ -415,7 +415,8 @@ int mh_profile_count(mh_ctx* ctx) {
     return (int)ctx->names.size();
 }
 
-int mh_profile_get(mh_ctx* ctx, int i, char* name, int name_cap, uint64_t* launches, double* total_ms) {
+int mh_profile_get(mh_ctx* ctx, int i, char* name, int name_cap, uint64_t* launches, double* total_ms,
+                   uint64_t* bytes) {
     if (!ctx || i < 0 || i >= (int)ctx->names.size()) return MH_EINVAL;
     drain_events(ctx, true);
     if (name && name_cap > 0) {
@@ -424,6 +425,7 @@ int mh_profile_get(mh_ctx* ctx, int i, char* name, int name_cap, uint64_t* launc
     }
     if (launches) *launches = ctx->stats[i].launches;
     if (total_ms) *total_ms = ctx->stats[i].total_ms;
+    if (bytes) *bytes = ctx->stats[i].bytes;
     return MH_OK;
 }
 

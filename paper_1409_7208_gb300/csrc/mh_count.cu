@@ -230,8 +230,8 @@ void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, 
     totals.zero();
     tile_out.zero();
     if (n)
-        MH_LAUNCH(ctx, "runs_count", (unsigned)tiles, kRunThreads, 0, runs_count_kernel<NW>, sorted, n, K1, d, spectrum,
-                  n_spectrum, tile_out.p, (unsigned long long*)totals.p, ctx->d_status);
+        MH_LAUNCH_B(ctx, "runs_count", n * 8 * NW, (unsigned)tiles, kRunThreads, 0, runs_count_kernel<NW>, sorted, n, K1,
+                    d, spectrum, n_spectrum, tile_out.p, (unsigned long long*)totals.p, ctx->d_status);
     exclusive_scan_u64(ctx, tile_out.p, tile_off.p, tiles);
     uint64_t tot[3];
     read_u64(ctx, tile_off.p + tiles, &tot[0], 1);
@@ -275,8 +275,8 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
     nwin.reset();
     Buf<uint64_t> keys(ctx, (n ? n : 1) * NW), alt(ctx, (n ? n : 1) * NW);
     if (n)
-        MH_LAUNCH(ctx, "extract_canonical", grid_for(ctx, F * 32, 256, 8), 256, 0, extract_canonical_kernel<NW>,
-                  reads->packed, reads->frag_offs, woff.p, F, k, keys.p);
+        MH_LAUNCH_B(ctx, "extract_canonical", reads->n_packed / 4 + n * 8 * NW, grid_for(ctx, F * 32, 256, 8), 256, 0,
+                    extract_canonical_kernel<NW>, reads->packed, reads->frag_offs, woff.p, F, k, keys.p);
     woff.reset();
     bool in_alt = radix_sort<NW>(ctx, keys.p, alt.p, nullptr, nullptr, n, 0, 2 * (k + 1));
     Buf<uint64_t>& spec = in_alt ? alt : keys;

@@ -41,6 +41,7 @@ void cuda_check(cudaError_t e, const char* what);
 struct KernelStat {
     uint64_t launches = 0;
     double total_ms = 0.0;
+    uint64_t bytes = 0;  // algorithmic bytes (reads + writes the kernel must do)
 };
 
 struct mh_ctx {
@@ -63,6 +64,7 @@ struct mh_ctx {
     struct Pending {
         int name;
         cudaEvent_t a, b;
+        uint64_t bytes;
     };
     std::vector<Pending> pending;
     std::vector<std::string> names;
@@ -148,8 +150,9 @@ struct Buf {
 struct Prof {
     mh_ctx* ctx;
     int id = -1;
+    uint64_t bytes = 0;
     cudaEvent_t a = nullptr, b = nullptr;
-    Prof(mh_ctx* c, const char* name);
+    Prof(mh_ctx* c, const char* name, uint64_t algo_bytes = 0);
     ~Prof();
 };
 
@@ -157,6 +160,14 @@ struct Prof {
 #define MH_LAUNCH(ctx, name, grid, block, smem, kernel, ...)                          \
     do {                                                                               \
         ::mh::Prof _mh_prof((ctx), (name));                                            \
+        kernel<<<(grid), (block), (smem), (ctx)->stream>>>(__VA_ARGS__);               \
+        ::mh::cuda_check(cudaGetLastError(), (name));                                  \
+    } while (0)
+
+// Same, also recording the launch's algorithmic bytes for the roofline.
+#define MH_LAUNCH_B(ctx, name, algo_bytes, grid, block, smem, kernel, ...)            \
+    do {                                                                               \
+        ::mh::Prof _mh_prof((ctx), (name), (algo_bytes));                              \
         kernel<<<(grid), (block), (smem), (ctx)->stream>>>(__VA_ARGS__);               \
         ::mh::cuda_check(cudaGetLastError(), (name));                                  \
     } while (0)

@@ -9,8 +9,12 @@
 // counts, looks back over earlier tiles' published counts (decoupled
 // look-back, every wait bounded), stages the tile in shared memory in digit
 // order and writes it out in coalesced runs.  Look-back counts are 30-bit,
-// so a pass runs in chunks of at most (2^18 - 1) tiles, each chunk with its
-// own look-back chain and digit offsets from the histogram.
+// so a pass runs in chunks of at most (2^18 - 1) tiles, one launch per chunk,
+// each with its own look-back chain.  Chunk 0 starts from the global digit
+// offsets of the histogram (the same for every pass); the last tile of chunk
+// c writes the digit offsets where chunk c+1 starts.
+#include <cstdlib>
+
 #include "mh_internal.cuh"
 
 namespace mh {
@@ -50,53 +54,40 @@ constexpr size_t onesweep_smem() {
 }
 
 // ------------------------------------------------------------ histogram
-// hist[(chunk * n_passes + p) * 256 + digit], digit of pass p = bits
-// [shift0 + 8p, +8).  grid.y = chunk, grid.x splits the chunk.
+// hist[p * 256 + digit] over all n keys, digit of pass p = bits
+// [shift0 + 8p, +8).
 template <int NW>
-__global__ void __launch_bounds__(256) radix_hist_kernel(const uint64_t* __restrict__ keys, uint64_t n,
-                                                         uint64_t chunk_len, int shift0, int n_passes,
-                                                         uint32_t* __restrict__ hist) {
+__global__ void __launch_bounds__(256) radix_hist_kernel(const uint64_t* __restrict__ keys, uint64_t n, int shift0,
+                                                         int n_passes, uint32_t* __restrict__ hist) {
     extern __shared__ uint32_t sh[];
     const int nb = n_passes * 256;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
     __syncthreads();
-    uint64_t c0 = (uint64_t)blockIdx.y * chunk_len;
-    uint64_t c1 = c0 + chunk_len < n ? c0 + chunk_len : n;
-    uint64_t len = c1 - c0;
-    uint64_t per = ceil_div(len, gridDim.x);
-    uint64_t b0 = c0 + per * blockIdx.x, b1 = b0 + per < c1 ? b0 + per : c1;
-    for (uint64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         Key<NW> k = load_key<NW>(keys, i);
         for (int p = 0; p < n_passes; p++) atomicAdd(&sh[p * 256 + key_digit<NW>(k, shift0 + 8 * p)], 1u);
     }
     __syncthreads();
-    uint32_t* out = hist + (uint64_t)blockIdx.y * nb;
     for (int i = threadIdx.x; i < nb; i += blockDim.x)
-        if (sh[i]) atomicAdd(&out[i], sh[i]);
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
-// base[(c * P + p) * 256 + d] = sum_{d' < d} total_p(d') + sum_{c' < c} hist[c'][p][d].
-// One block of 256 threads per pass.
-__global__ void radix_base_kernel(const uint32_t* __restrict__ hist, int n_chunks, int n_passes,
-                                  uint64_t* __restrict__ base) {
+// base[p * 256 + d] = sum over d' < d of hist[p][d'] (where chunk 0 of pass
+// p starts writing digit d).  One block of 256 threads per pass.
+__global__ void radix_base_kernel(const uint32_t* __restrict__ hist, uint64_t* __restrict__ base,
+                                  uint64_t base_stride) {
     __shared__ uint64_t s[256];
     int p = blockIdx.x, d = threadIdx.x;
-    uint64_t tot = 0;
-    for (int c = 0; c < n_chunks; c++) tot += hist[((uint64_t)c * n_passes + p) * 256 + d];
+    uint64_t tot = hist[p * 256 + d];
     s[d] = tot;
     __syncthreads();
-    // exclusive scan over 256 digits (simple, once per pass)
     for (int off = 1; off < 256; off <<= 1) {
         uint64_t v = d >= off ? s[d - off] : 0;
         __syncthreads();
         s[d] += v;
         __syncthreads();
     }
-    uint64_t run = s[d] - tot;
-    for (int c = 0; c < n_chunks; c++) {
-        base[((uint64_t)c * n_passes + p) * 256 + d] = run;
-        run += hist[((uint64_t)c * n_passes + p) * 256 + d];
-    }
+    base[p * base_stride + d] = s[d] - tot;
 }
 
 // --------------------------------------------------------------- onesweep
@@ -104,8 +95,8 @@ template <int NW, bool HV>
 __global__ void __launch_bounds__(kSortThreads, 2)
     onesweep_kernel(const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout, const uint32_t* __restrict__ vin,
                     uint32_t* __restrict__ vout, uint64_t n, int shift, const uint64_t* __restrict__ digit_base,
-                    uint32_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
-                    uint32_t* __restrict__ err) {
+                    uint64_t* __restrict__ next_base, uint32_t* __restrict__ status,
+                    uint32_t* __restrict__ tile_counter, uint32_t* __restrict__ err) {
     constexpr int ITEMS = SortItems<NW>::v;
     constexpr int TILE = sort_tile<NW>();
     extern __shared__ __align__(16) unsigned char smem[];
@@ -213,6 +204,8 @@ __global__ void __launch_bounds__(kSortThreads, 2)
         st_relaxed_u32(st, kFlagInc | (uint32_t)((excl + cnt) & kCountMask));
     }
     scatter_base[d] = digit_base[d] + excl - tile_start[d];
+    // the chunk's last tile: where the next chunk starts writing digit d
+    if (next_base && (uint64_t)(tile + 1) * TILE >= n) next_base[d] = digit_base[d] + excl + cnt;
     __syncthreads();
     // stage in tile digit order
 #pragma unroll
@@ -240,26 +233,33 @@ __global__ void __launch_bounds__(kSortThreads, 2)
     }
 }
 
+// Tiles per look-back chunk: (2^18 - 1), or MH_SORT_CHUNK_TILES (>= 1) when
+// set, which tests use to run the multi-chunk path on small inputs.
+static uint64_t chunk_tiles() {
+    static uint64_t v = [] {
+        const char* e = std::getenv("MH_SORT_CHUNK_TILES");
+        uint64_t t = e ? std::strtoull(e, nullptr, 10) : 0;
+        return (t >= 1 && t <= kMaxTilesPerChunk) ? t : kMaxTilesPerChunk;
+    }();
+    return v;
+}
+
 template <int NW, bool HV>
 static bool radix_sort_impl(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt, uint64_t n,
                             int bit_lo, int bit_hi) {
     if (n <= 1 || bit_hi <= bit_lo) return false;
     constexpr int TILE = sort_tile<NW>();
     const int n_passes = (bit_hi - bit_lo + 7) / 8;
-    const uint64_t chunk_len = kMaxTilesPerChunk * TILE;
+    const uint64_t chunk_len = chunk_tiles() * TILE;
     const int n_chunks = (int)ceil_div(n, chunk_len);
-    Buf<uint32_t> hist(ctx, (size_t)n_chunks * n_passes * 256);
-    Buf<uint64_t> base(ctx, (size_t)n_chunks * n_passes * 256);
+    Buf<uint32_t> hist(ctx, (size_t)n_passes * 256);
+    // base[(p * n_chunks + c) * 256 + d]: where chunk c of pass p starts writing digit d
+    Buf<uint64_t> base(ctx, (size_t)n_passes * n_chunks * 256);
     hist.zero();
-    {
-        dim3 grid((unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(std::min(n, chunk_len), 256 * 32),
-                                                                     (uint64_t)ctx->num_sms * 4)),
-                  (unsigned)n_chunks);
-        MH_LAUNCH(ctx, "radix_hist", grid, 256, sizeof(uint32_t) * n_passes * 256, radix_hist_kernel<NW>, keys, n,
-                  chunk_len, bit_lo, n_passes, hist.p);
-    }
-    MH_LAUNCH(ctx, "radix_base", n_passes, 256, 0, radix_base_kernel, hist.p, n_chunks, n_passes, base.p);
-    const uint64_t max_tiles = std::min<uint64_t>(kMaxTilesPerChunk, ceil_div(n, TILE));
+    MH_LAUNCH_B(ctx, "radix_hist", n * 8 * NW, grid_for(ctx, n, 256, 4), 256, sizeof(uint32_t) * n_passes * 256,
+                radix_hist_kernel<NW>, keys, n, bit_lo, n_passes, hist.p);
+    MH_LAUNCH(ctx, "radix_base", n_passes, 256, 0, radix_base_kernel, hist.p, base.p, (uint64_t)n_chunks * 256);
+    const uint64_t max_tiles = std::min<uint64_t>(chunk_tiles(), ceil_div(n, TILE));
     Buf<uint32_t> status(ctx, max_tiles * 256);
     Buf<uint32_t> counter(ctx, 64);
     constexpr size_t smem = onesweep_smem<NW, HV>();
@@ -273,9 +273,11 @@ static bool radix_sort_impl(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t
             uint64_t tiles = ceil_div(len, TILE);
             MH_CUDA(cudaMemsetAsync(status.p, 0, tiles * 256 * sizeof(uint32_t), ctx->stream));
             MH_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(uint32_t), ctx->stream));
-            MH_LAUNCH(ctx, "radix_onesweep", (unsigned)tiles, kSortThreads, smem, (onesweep_kernel<NW, HV>),
-                      kin + c0 * NW, kout, HV ? vin + c0 : nullptr, vout, len, bit_lo + 8 * p,
-                      base.p + ((uint64_t)c * n_passes + p) * 256, status.p, counter.p, ctx->d_status);
+            MH_LAUNCH_B(ctx, "radix_onesweep", len * (16 * NW + (HV ? 8 : 0)), (unsigned)tiles, kSortThreads, smem,
+                        (onesweep_kernel<NW, HV>), kin + c0 * NW, kout, HV ? vin + c0 : nullptr, vout, len,
+                        bit_lo + 8 * p, base.p + ((uint64_t)p * n_chunks + c) * 256,
+                        c + 1 < n_chunks ? base.p + ((uint64_t)p * n_chunks + c + 1) * 256 : nullptr, status.p,
+                        counter.p, ctx->d_status);
         }
         std::swap(kin, kout);
         std::swap(vin, vout);

@@ -1,0 +1,41 @@
+"""The radix sort's multi-chunk path (several look-back chains per pass, digit
+offsets carried between chunks) on inputs small enough for the oracle: the
+library is run in a child process with 3 tiles per chunk."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CHILD = r"""
+import sys, numpy as np
+sys.path.insert(0, %r)
+import oracle, synth, paper_1409_7208_gb300 as mh
+ctx = mh.Context(device=0)
+for seed, k, n_reads in ((1, 21, 3000), (2, 31, 2500), (3, 47, 1500), (4, 99, 900)):
+    ascii, offs = synth.uniform_genome_reads(seed, 4000, n_reads, 150, 0.01)
+    reads = mh.mh_pack_reads(ctx, ascii, offs)
+    s = mh.mh_count_kmers(ctx, reads, k, 2)
+    m = mh.mh_mercy_kmers(ctx, reads, s)
+    g = mh.mh_build_sdbg(ctx, s, m)
+    w = oracle.count(ascii, offs, k, 2, mercy=True)
+    wg = oracle.build_sdbg(k, w["solid_keys"], w["solid_cnt"], w["mercy_keys"], w["mercy_cnt"])
+    gs, gm, gg = s.numpy(), m.numpy(), g.numpy()
+    assert np.array_equal(gs["keys"], w["solid_keys"]) and np.array_equal(gs["counts"], w["solid_cnt"])
+    assert np.array_equal(gm["keys"], w["mercy_keys"]) and np.array_equal(gm["counts"], w["mercy_cnt"])
+    for key in ("W", "last", "dummy", "F", "aux"):
+        assert np.array_equal(gg[key], wg[key]), key
+print("ok")
+""" % ROOT
+
+
+@pytest.mark.parametrize("tiles", ["1", "3"])
+def test_multi_chunk_sort_matches_oracle(tiles):
+    env = dict(os.environ, MH_SORT_CHUNK_TILES=tiles)
+    p = subprocess.run([sys.executable, "-c", CHILD], env=env, capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stdout + p.stderr
+    assert "ok" in p.stdout
