@@ -191,6 +191,32 @@ typedef struct {
 int mh_sdbg_view_get(const mh_sdbg* g, mh_sdbg_view* v);
 void mh_free_sdbg(mh_sdbg* g);
 
+/* ------------------------------------------------- no-allocation sort */
+
+/* Sort n keys (nw = 1, 2 or 4 words each, layout as above) ascending by their
+ * low key_bits bits (1 <= key_bits <= 64 * nw; higher bits must be zero),
+ * reading keys_in and writing keys_out (distinct device buffers of n * nw
+ * words on the calling thread's current device), on `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  The paper has no
+ * counterpart: this is the library's radix sort, offered to callers that may
+ * not allocate device memory at all - hosts that own the device's whole
+ * memory budget, or code that must never enter the driver's allocator or
+ * synchronise the device the way cudaFree does.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine; all scratch space is one static
+ * device array of about 17 MiB that every device loading the library keeps
+ * until exit.
+ *   * limit: n * nw <= 2^21 words (16 MiB of keys); larger inputs return
+ *     MH_EOVERFLOW and touch nothing;
+ *   * the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   * every call on a device shares the array and clears what must start at
+ *     zero itself; calls that overlap on the GPU race and must be avoided;
+ *   * the call waits for `stream` at the end to read a status word.
+ * Errors: MH_EINVAL (nw, key_bits, NULL or identical buffers), MH_EOVERFLOW,
+ * MH_ETIMEOUT (a bounded look-back wait ran out), MH_EDEVICE. */
+int mh_sort_keys_noalloc(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n, int nw, int key_bits,
+                         void* stream);
+
 /* ------------------------------------------------------------ utilities */
 
 const char* mh_strerror(int code);

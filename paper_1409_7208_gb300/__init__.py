@@ -34,6 +34,7 @@ SYMBOLS = (
     "mh_count_kmers", "mh_mercy_kmers", "mh_kmers_view_get", "mh_free_kmers", "mh_build_sdbg",
     "mh_sdbg_view_get", "mh_free_sdbg", "mh_strerror", "mh_last_error_message", "mh_stream",
     "mh_memory", "mh_profile_count", "mh_profile_get", "mh_profile_reset", "mh_set_profile",
+    "mh_sort_keys_noalloc",
 )
 
 
@@ -109,6 +110,7 @@ def load_library(path: str = LIB_PATH):
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64)]
     lib.mh_profile_reset.argtypes = [P]
     lib.mh_set_profile.argtypes = [P, ctypes.c_int]
+    lib.mh_sort_keys_noalloc.argtypes = [P, P, u64, ctypes.c_int, ctypes.c_int, P]
     _lib = lib
     return lib
 
@@ -393,3 +395,21 @@ def mh_build_sdbg(ctx: Context, solid: Kmers, mercy: Kmers | None = None) -> Sdb
     ctx._check(ctx._lib.mh_build_sdbg(ctx._h, solid._h, mercy._h if mercy is not None else None,
                                       ctypes.byref(h)))
     return Sdbg(ctx, h)
+
+
+def mh_sort_keys_noalloc(keys_in, keys_out, nw: int, key_bits: int, stream=None) -> None:
+    """Sort device keys without any device allocation (the C entry point of
+    the same name): for callers that must not allocate, e.g. inside an engine
+    that owns all device memory.  ``keys_in``/``keys_out``: CUDA tensors of
+    n * nw int64 (uint64 bits), distinct; n * nw <= 2^21.  The first call per
+    device looks up the library's static scratch array; overlapping calls
+    race on that array."""
+    import torch
+    lib = load_library()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    n = keys_in.numel() // nw
+    rc = lib.mh_sort_keys_noalloc(keys_in.data_ptr(), keys_out.data_ptr(), n, int(nw), int(key_bits),
+                                  stream.cuda_stream)
+    if rc != MH_OK:
+        raise MhError(rc, "mh_sort_keys_noalloc")

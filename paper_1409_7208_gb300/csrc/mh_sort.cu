@@ -15,223 +15,9 @@
 // c writes the digit offsets where chunk c+1 starts.
 #include <cstdlib>
 
-#include "mh_internal.cuh"
+#include "mh_sort_kernels.cuh"
 
 namespace mh {
-
-constexpr int kSortThreads = 256;
-constexpr int kSortWarps = kSortThreads / 32;
-constexpr uint64_t kMaxTilesPerChunk = (1ull << 18) - 1;
-constexpr uint32_t kFlagAgg = 1u << 30;
-constexpr uint32_t kFlagInc = 2u << 30;
-constexpr uint32_t kCountMask = (1u << 30) - 1;
-constexpr int kSpinLimit = 1 << 23;
-
-template <int NW>
-struct SortItems;
-template <>
-struct SortItems<1> {
-    static constexpr int v = 16;
-};
-template <>
-struct SortItems<2> {
-    static constexpr int v = 10;
-};
-template <>
-struct SortItems<4> {
-    static constexpr int v = 6;
-};
-
-template <int NW>
-__host__ __device__ constexpr int sort_tile() {
-    return kSortThreads * SortItems<NW>::v;
-}
-
-template <int NW, bool HV>
-constexpr size_t onesweep_smem() {
-    return sizeof(uint32_t) * (kSortWarps * 256 + 256 + 256 + 8) + sizeof(uint64_t) * 256 +
-           sizeof(uint64_t) * NW * sort_tile<NW>() + (HV ? sizeof(uint32_t) * sort_tile<NW>() : 0);
-}
-
-// ------------------------------------------------------------ histogram
-// hist[p * 256 + digit] over all n keys, digit of pass p = bits
-// [shift0 + 8p, +8).
-template <int NW>
-__global__ void __launch_bounds__(256) radix_hist_kernel(const uint64_t* __restrict__ keys, uint64_t n, int shift0,
-                                                         int n_passes, uint32_t* __restrict__ hist) {
-    extern __shared__ uint32_t sh[];
-    const int nb = n_passes * 256;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
-    __syncthreads();
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        Key<NW> k = load_key<NW>(keys, i);
-        for (int p = 0; p < n_passes; p++) atomicAdd(&sh[p * 256 + key_digit<NW>(k, shift0 + 8 * p)], 1u);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += blockDim.x)
-        if (sh[i]) atomicAdd(&hist[i], sh[i]);
-}
-
-// base[p * 256 + d] = sum over d' < d of hist[p][d'] (where chunk 0 of pass
-// p starts writing digit d).  One block of 256 threads per pass.
-__global__ void radix_base_kernel(const uint32_t* __restrict__ hist, uint64_t* __restrict__ base,
-                                  uint64_t base_stride) {
-    __shared__ uint64_t s[256];
-    int p = blockIdx.x, d = threadIdx.x;
-    uint64_t tot = hist[p * 256 + d];
-    s[d] = tot;
-    __syncthreads();
-    for (int off = 1; off < 256; off <<= 1) {
-        uint64_t v = d >= off ? s[d - off] : 0;
-        __syncthreads();
-        s[d] += v;
-        __syncthreads();
-    }
-    base[p * base_stride + d] = s[d] - tot;
-}
-
-// --------------------------------------------------------------- onesweep
-template <int NW, bool HV>
-__global__ void __launch_bounds__(kSortThreads, 2)
-    onesweep_kernel(const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout, const uint32_t* __restrict__ vin,
-                    uint32_t* __restrict__ vout, uint64_t n, int shift, const uint64_t* __restrict__ digit_base,
-                    uint64_t* __restrict__ next_base, uint32_t* __restrict__ status,
-                    uint32_t* __restrict__ tile_counter, uint32_t* __restrict__ err) {
-    constexpr int ITEMS = SortItems<NW>::v;
-    constexpr int TILE = sort_tile<NW>();
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* warp_hist = reinterpret_cast<uint32_t*>(smem);          // [warps][256]
-    uint32_t* tile_cnt = warp_hist + kSortWarps * 256;                 // [256]
-    uint32_t* tile_start = tile_cnt + 256;                             // [256]
-    uint32_t* misc = tile_start + 256;                                 // [8]
-    uint64_t* scatter_base = reinterpret_cast<uint64_t*>(misc + 8);    // [256]
-    uint64_t* stage = scatter_base + 256;                              // [NW][TILE]
-    uint32_t* vstage = reinterpret_cast<uint32_t*>(stage + NW * TILE); // [TILE]
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) misc[0] = atomicAdd(tile_counter, 1u);
-    for (int i = tid; i < kSortWarps * 256; i += kSortThreads) warp_hist[i] = 0;
-    __syncthreads();
-    const uint32_t tile = misc[0];
-    const uint64_t tile_base = (uint64_t)tile * TILE;
-
-    // load: warp-striped, item i of lane l is key tile_base + warp*32*ITEMS + 32*i + l
-    Key<NW> k[ITEMS];
-    uint32_t v[HV ? ITEMS : 1];
-    uint32_t rank[ITEMS];
-    const uint64_t wbase = tile_base + (uint64_t)warp * 32 * ITEMS;
-#pragma unroll
-    for (int i = 0; i < ITEMS; i++) {
-        uint64_t idx = wbase + 32 * i + lane;
-        if (idx < n) {
-            k[i] = load_key<NW>(kin, idx);
-            if constexpr (HV) v[i] = vin[idx];
-        } else {
-#pragma unroll
-            for (int w = 0; w < NW; w++) k[i].w[w] = 0;
-            if constexpr (HV) v[i] = 0;
-        }
-    }
-    // rank within the warp, stable by item then lane
-    uint32_t* wh = warp_hist + warp * 256;
-    const uint32_t lt_mask = (1u << lane) - 1;
-#pragma unroll
-    for (int i = 0; i < ITEMS; i++) {
-        uint64_t idx = wbase + 32 * i + lane;
-        uint32_t dg = idx < n ? key_digit<NW>(k[i], shift) : 256u;
-        uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg);
-        int leader = __ffs(peers) - 1;
-        uint32_t old = 0;
-        if (lane == leader && dg < 256u) {
-            old = wh[dg];
-            wh[dg] = old + __popc(peers);
-        }
-        old = __shfl_sync(0xFFFFFFFFu, old, leader);
-        rank[i] = old + __popc(peers & lt_mask);
-        __syncwarp();
-    }
-    __syncthreads();
-    // per digit: exclusive prefix over warps, tile total
-    const int d = tid;  // kSortThreads == 256
-    uint32_t cnt = 0;
-#pragma unroll
-    for (int w = 0; w < kSortWarps; w++) {
-        uint32_t c = warp_hist[w * 256 + d];
-        warp_hist[w * 256 + d] = cnt;
-        cnt += c;
-    }
-    tile_cnt[d] = cnt;
-    // publish this tile's count early so later tiles can proceed
-    uint32_t* st = status + (uint64_t)tile * 256 + d;
-    st_relaxed_u32(st, (tile == 0 ? kFlagInc : kFlagAgg) | cnt);
-    // block exclusive scan of tile_cnt -> tile_start
-    {
-        uint32_t x = cnt;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
-            if (lane >= off) x += y;
-        }
-        if (lane == 31) misc[warp] = x;  // misc[0..7]; misc[0] (tile) already read
-        __syncthreads();
-        uint32_t wpre = 0;
-        for (int w = 0; w < warp; w++) wpre += misc[w];
-        tile_start[d] = wpre + x - cnt;
-    }
-    // look back over earlier tiles for this digit
-    uint64_t excl = 0;
-    if (tile > 0) {
-        int64_t j = (int64_t)tile - 1;
-        bool ok = true;
-        while (j >= 0) {
-            const uint32_t* sp = status + (uint64_t)j * 256 + d;
-            uint32_t s = ld_relaxed_u32(sp);
-            int spins = 0;
-            while ((s & ~kCountMask) == 0) {
-                if (++spins > kSpinLimit) {
-                    ok = false;
-                    break;
-                }
-                if (spins > 64) __nanosleep(128);
-                s = ld_relaxed_u32(sp);
-            }
-            if (!ok) break;
-            excl += s & kCountMask;
-            if ((s & ~kCountMask) == kFlagInc) break;
-            j--;
-        }
-        if (!ok) atomicOr(err, ST_SPIN_TIMEOUT);
-        st_relaxed_u32(st, kFlagInc | (uint32_t)((excl + cnt) & kCountMask));
-    }
-    scatter_base[d] = digit_base[d] + excl - tile_start[d];
-    // the chunk's last tile: where the next chunk starts writing digit d
-    if (next_base && (uint64_t)(tile + 1) * TILE >= n) next_base[d] = digit_base[d] + excl + cnt;
-    __syncthreads();
-    // stage in tile digit order
-#pragma unroll
-    for (int i = 0; i < ITEMS; i++) {
-        uint64_t idx = wbase + 32 * i + lane;
-        if (idx < n) {
-            uint32_t dg = key_digit<NW>(k[i], shift);
-            uint32_t pos = tile_start[dg] + warp_hist[warp * 256 + dg] + rank[i];
-#pragma unroll
-            for (int w = 0; w < NW; w++) stage[w * TILE + pos] = k[i].w[w];
-            if constexpr (HV) vstage[pos] = v[i];
-        }
-    }
-    __syncthreads();
-    const uint64_t rem = n - tile_base;
-    const int n_valid = rem < (uint64_t)TILE ? (int)rem : TILE;
-    for (int j = tid; j < n_valid; j += kSortThreads) {
-        Key<NW> kk;
-#pragma unroll
-        for (int w = 0; w < NW; w++) kk.w[w] = stage[w * TILE + j];
-        uint32_t dg = key_digit<NW>(kk, shift);
-        uint64_t dst = scatter_base[dg] + j;
-        store_key<NW>(kout, dst, kk);
-        if constexpr (HV) vout[dst] = vstage[j];
-    }
-}
 
 // Tiles per look-back chunk: (2^18 - 1), or MH_SORT_CHUNK_TILES (>= 1) when
 // set, which tests use to run the multi-chunk path on small inputs.
