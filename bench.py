@@ -46,14 +46,14 @@ WORKLOADS = {
                 "lognormal abundances, sigma 1.5), 10M pairs 2x150 bp, 3' error ramp to 1% (mean 0.5%), "
                 "k=31, d=2, mercy on",
         "k": 31, "d": 2, "seed": 2,
-        "gen": lambda seed: __import__("synth").metagenome_reads(seed=seed),
+        "gen": lambda seed, pairs=10_000_000: __import__("synth").metagenome_reads(seed=seed, n_pairs=pairs),
         "sample": lambda seed, n: __import__("synth").metagenome_reads(seed=seed, n_pairs=n // 2),
     },
     "plain": {
         "name": "plain single job: uniform 50 kbp genome, 10,000 x 100 bp single-end reads, 1% errors, "
                 "k=21, d=2, mercy on",
         "k": 21, "d": 2, "seed": 1,
-        "gen": lambda seed: __import__("synth").uniform_genome_reads(seed=seed),
+        "gen": lambda seed, pairs=None: __import__("synth").uniform_genome_reads(seed=seed),
         "sample": lambda seed, n: __import__("synth").uniform_genome_reads(seed=seed, n_reads=min(n, 10_000)),
     },
 }
@@ -68,6 +68,8 @@ def _args():
     p.add_argument("--workload", default="metagenome", choices=sorted(WORKLOADS))
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--pairs", type=int, default=10_000_000,
+                   help="read pairs of the metagenome workload (smaller values: profiling cases only)")
     return p.parse_args()
 
 
@@ -204,7 +206,7 @@ def main():
             dist.barrier()
 
     k, d = wl["k"], wl["d"]
-    ascii, offs = wl["gen"](wl["seed"] + 1000 * rank)
+    ascii, offs = wl["gen"](wl["seed"] + 1000 * rank, args.pairs)
     n_bases = len(ascii)
     stream = torch.cuda.current_stream()
     ctx = mh.Context(device=local, stream=stream)
@@ -293,20 +295,22 @@ def main():
         stream.synchronize()
         d2h["bytes"] = nbytes + 48  # + F, returned by value
 
-    step(pin_ascii, pin_offs, None, download)  # warm the host path
-    torch.cuda.synchronize()
-    barrier()
-    e0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        step(pin_ascii, pin_offs, None, download)
-    torch.cuda.synchronize()
-    e_s = time.perf_counter() - e0
-    if dist is not None:
-        t = torch.tensor([e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_s = float(t.item())
-    e2e = {"value": n_kmers * world * args.e2e_steps / e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(n_bases + offs.nbytes), "d2h_bytes_per_step": int(d2h["bytes"])}
+    e2e = None
+    if args.e2e_steps > 0:
+        step(pin_ascii, pin_offs, None, download)  # warm the host path
+        torch.cuda.synchronize()
+        barrier()
+        e0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            step(pin_ascii, pin_offs, None, download)
+        torch.cuda.synchronize()
+        e_s = time.perf_counter() - e0
+        if dist is not None:
+            t = torch.tensor([e_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_s = float(t.item())
+        e2e = {"value": n_kmers * world * args.e2e_steps / e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(n_bases + offs.nbytes), "d2h_bytes_per_step": int(d2h["bytes"])}
 
     # roofline of the dominant kernel (radix scatter pass)
     peak, peak_kind = _peak_hbm()

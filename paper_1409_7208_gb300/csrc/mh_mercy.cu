@@ -1,18 +1,23 @@
 // mh_mercy_kmers: mercy (k+1)-mers (paper, Sec. 2, third paragraph).
 //
-//   degrees  for each canonical solid edge c: out0(c) = no solid edge starts
-//            with c[1..k]; in0(c) = no solid edge ends with c[0..k-1], i.e. no
-//            solid edge starts with rc(c)[1..k] (the solid set is closed under
-//            reverse complement).  Both are one lower-bound search in the
-//            sorted solid table.
-//   table    open-addressing hash set of the canonical solid edges with the
-//            two flags (linear probing, 32-bit tags, load <= 1/2).
-//   scan     warp per fragment, 32 windows at a time: lookup of each window,
-//            ballot of the solid ones, previous solid position by bit scan
-//            (carried across rounds); a solid window q whose previous solid
-//            window p has no outdegree, with q > p+1 and no indegree at q,
-//            emits the canonical keys of windows p+1..q-1.
-//   finish   sort + dedup of the canonical candidates, counts looked up in the
+//   degrees  for every solid edge x (both orientations are in the sorted
+//            solid table S): out0(x) = no solid edge starts with x[1..k];
+//            in0(x) = no solid edge ends with x[0..k-1], i.e. none of
+//            c x[0..k-1] (c in ACGT) is solid.  Each thread takes 16
+//            consecutive entries of S; for entries with the same first
+//            symbol the queries ascend with x, so every lower-bound search
+//            gallops from the previous answer and stays in cache.
+//   ends     the edges with out0 or in0 (the graph's dead ends, a small
+//            fraction of S) go into a small open-addressing hash table with
+//            their two flags, which stays in L2.
+//   probe    warp per fragment, one window per lane: a probe of the small
+//            table per window; every window p without outdegree is recorded
+//            as a hit (its position and the end of its fragment).
+//   walk     thread per hit: step forward to the next solid window q (probes
+//            of a hash set of the canonical solid keys); if q > p+1 and q
+//            has no indegree, the windows p+1..q-1 are emitted (canonical
+//            keys).
+//   finish   sort + dedup of the candidates, counts looked up in the
 //            counting spectrum, both strands, sorted.
 #include "mh_internal.cuh"
 
@@ -25,41 +30,109 @@ struct Slot {
     uint32_t flags;
 };
 
-// First index in the sorted table with key >= q.
+// First index in [0, n) with a[i] >= q, searched outward from `hint` (any
+// value in [0, n]): exponential steps towards the answer, then bisection.
 template <int NW>
-__device__ __forceinline__ uint64_t lower_bound_keys(const uint64_t* __restrict__ a, uint64_t n, const Key<NW>& q) {
-    uint64_t lo = 0, hi = n;
+__device__ __forceinline__ uint64_t gallop_lb(const uint64_t* __restrict__ a, uint64_t n, const Key<NW>& q,
+                                              uint64_t hint) {
+    uint64_t lo, hi;  // answer in [lo, hi]
+    if (hint < n && key_less<NW>(load_key<NW>(a, hint), q)) {
+        // a[hint] < q: answer > hint
+        lo = hint + 1;
+        uint64_t step = 1;
+        while (true) {
+            uint64_t probe = lo + step - 1;
+            if (probe >= n) {
+                hi = n;
+                break;
+            }
+            if (!key_less<NW>(load_key<NW>(a, probe), q)) {
+                hi = probe;
+                break;
+            }
+            lo = probe + 1;
+            step <<= 1;
+        }
+    } else {
+        // a[hint] >= q (or hint == n): answer <= hint
+        hi = hint;
+        uint64_t step = 1;
+        while (true) {
+            if (hi < step) {
+                lo = 0;
+                break;
+            }
+            uint64_t probe = hi - step;
+            if (key_less<NW>(load_key<NW>(a, probe), q)) {
+                lo = probe + 1;
+                break;
+            }
+            hi = probe;
+            step <<= 1;
+        }
+    }
     while (lo < hi) {
-        uint64_t mid = (lo + hi) >> 1;
+        uint64_t mid = lo + (hi - lo) / 2;
         if (key_less<NW>(load_key<NW>(a, mid), q)) lo = mid + 1; else hi = mid;
     }
     return lo;
 }
 
-// Is there a solid (k+1)-mer whose k-prefix is P (a k-symbol key)?
-template <int NW>
-__device__ __forceinline__ bool has_prefix(const uint64_t* __restrict__ solid, uint64_t S, const Key<NW>& P) {
-    Key<NW> q = key_shl<NW>(P, 2);  // P followed by A: the smallest edge with that prefix
-    uint64_t lb = lower_bound_keys<NW>(solid, S, q);
-    if (lb >= S) return false;
-    return key_eq<NW>(key_shr<NW>(load_key<NW>(solid, lb), 2), P);
-}
-
 __device__ __forceinline__ uint32_t slot_tag(uint64_t h) { return (uint32_t)(h >> 32) | 1u; }
 
-// For each canonical solid edge: degree flags, then insertion.
+constexpr int kDegreeRun = 16;  // consecutive solid entries per thread
+
+// flags[i]: bit0 out0(S[i]), bit1 in0(S[i]); counts the entries with a flag.
 template <int NW>
-__global__ void __launch_bounds__(256) degree_insert_kernel(const uint64_t* __restrict__ solid, uint64_t S, int k,
-                                                            Slot<NW>* __restrict__ table, uint64_t cap_mask,
-                                                            unsigned long long* __restrict__ n_out0,
-                                                            uint32_t* __restrict__ err) {
-    const int K1 = k + 1;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S; i += (uint64_t)gridDim.x * blockDim.x) {
-        Key<NW> x = load_key<NW>(solid, i);
-        Key<NW> r = key_rc<NW>(x, K1);
-        if (key_less<NW>(r, x)) continue;  // only the canonical orientation
-        bool out0 = !has_prefix<NW>(solid, S, key_low<NW>(x, 2 * k));
-        bool in0 = !has_prefix<NW>(solid, S, key_low<NW>(r, 2 * k));
+__global__ void __launch_bounds__(256) degree_kernel(const uint64_t* __restrict__ S, uint64_t n, int k,
+                                                     uint8_t* __restrict__ flags,
+                                                     unsigned long long* __restrict__ n_ends) {
+    uint32_t ends = 0;
+    for (uint64_t i0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) * kDegreeRun; i0 < n;
+         i0 += (uint64_t)gridDim.x * blockDim.x * kDegreeRun) {
+        uint64_t hint_out = n / 2, hint_in[4] = {n / 2, n / 2, n / 2, n / 2};
+        uint64_t i1 = i0 + kDegreeRun < n ? i0 + kDegreeRun : n;
+        for (uint64_t i = i0; i < i1; i++) {
+            Key<NW> x = load_key<NW>(S, i);
+            // out0: is there an edge x[1..k] c?  smallest candidate x[1..k] A
+            Key<NW> suf = key_low<NW>(x, 2 * k);
+            Key<NW> qo = key_shl<NW>(suf, 2);
+            uint64_t lb = gallop_lb<NW>(S, n, qo, hint_out);
+            hint_out = lb;
+            bool has_out = lb < n && key_eq<NW>(key_shr<NW>(load_key<NW>(S, lb), 2), suf);
+            // in0: is there an edge c x[0..k-1] for some c?
+            Key<NW> pre = key_shr<NW>(x, 2);
+            bool has_in = false;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                Key<NW> cc = key_zero<NW>();
+                cc.w[0] = (uint64_t)c;
+                Key<NW> qi = key_shl<NW>(cc, 2 * k);
+#pragma unroll
+                for (int w = 0; w < NW; w++) qi.w[w] |= pre.w[w];
+                uint64_t li = gallop_lb<NW>(S, n, qi, hint_in[c]);
+                hint_in[c] = li;
+                has_in |= li < n && key_eq<NW>(load_key<NW>(S, li), qi);
+            }
+            uint8_t f = (has_out ? 0 : 1) | (has_in ? 0 : 2);
+            flags[i] = f;
+            ends += f != 0;
+        }
+    }
+    for (int off = 16; off; off >>= 1) ends += __shfl_xor_sync(0xFFFFFFFFu, ends, off);
+    if ((threadIdx.x & 31) == 0 && ends) atomicAdd(n_ends, (unsigned long long)ends);
+}
+
+// Dead-end edges (oriented) with their flags into the small table.
+template <int NW>
+__global__ void __launch_bounds__(256) ends_insert_kernel(const uint64_t* __restrict__ S, uint64_t n,
+                                                          const uint8_t* __restrict__ flags,
+                                                          Slot<NW>* __restrict__ table, uint64_t cap_mask,
+                                                          uint32_t* __restrict__ err) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint8_t f = flags[i];
+        if (!f) continue;
+        Key<NW> x = load_key<NW>(S, i);
         uint64_t h = key_hash<NW>(x);
         uint32_t tag = slot_tag(h);
         uint64_t s = h & cap_mask;
@@ -68,45 +141,89 @@ __global__ void __launch_bounds__(256) degree_insert_kernel(const uint64_t* __re
             if (atomicCAS(&table[s].tag, 0u, tag) == 0u) {
 #pragma unroll
                 for (int w = 0; w < NW; w++) table[s].k[w] = x.w[w];
-                table[s].flags = (out0 ? 1u : 0u) | (in0 ? 2u : 0u);
+                table[s].flags = f;
                 placed = true;
                 break;
             }
             s = (s + 1) & cap_mask;
         }
         if (!placed) atomicOr(err, ST_TABLE_FULL);
-        if (out0) atomicAdd(n_out0, 1ull);
     }
 }
 
-// Flags of canonical key c (bit0 out0, bit1 in0), or -1 if c is not solid.
+// Flags of the oriented key x if it is a dead-end edge, else 0.
 template <int NW>
-__device__ __forceinline__ int table_find(const Slot<NW>* __restrict__ table, uint64_t cap_mask, const Key<NW>& c) {
-    uint64_t h = key_hash<NW>(c);
+__device__ __forceinline__ uint32_t ends_find(const Slot<NW>* __restrict__ table, uint64_t cap_mask,
+                                              const Key<NW>& x) {
+    uint64_t h = key_hash<NW>(x);
     uint32_t tag = slot_tag(h);
     uint64_t s = h & cap_mask;
     for (uint64_t probe = 0; probe <= cap_mask; probe++) {
         uint32_t t = table[s].tag;
-        if (t == 0u) return -1;
+        if (t == 0u) return 0;
         if (t == tag) {
             bool eq = true;
 #pragma unroll
-            for (int w = 0; w < NW; w++) eq &= table[s].k[w] == c.w[w];
-            if (eq) return (int)table[s].flags;
+            for (int w = 0; w < NW; w++) eq &= table[s].k[w] == x.w[w];
+            if (eq) return table[s].flags;
         }
         s = (s + 1) & cap_mask;
     }
-    return -1;
+    return 0;
+}
+
+// Canonical solid keys into the solidity set (tags and keys, no flags).
+template <int NW>
+__global__ void __launch_bounds__(256) solid_insert_kernel(const uint64_t* __restrict__ S, uint64_t n, int K1,
+                                                           Slot<NW>* __restrict__ table, uint64_t cap_mask,
+                                                           uint32_t* __restrict__ err) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        Key<NW> x = load_key<NW>(S, i);
+        if (key_less<NW>(key_rc<NW>(x, K1), x)) continue;
+        uint64_t h = key_hash<NW>(x);
+        uint32_t tag = slot_tag(h);
+        uint64_t s = h & cap_mask;
+        bool placed = false;
+        for (uint64_t probe = 0; probe <= cap_mask; probe++) {
+            if (atomicCAS(&table[s].tag, 0u, tag) == 0u) {
+#pragma unroll
+                for (int w = 0; w < NW; w++) table[s].k[w] = x.w[w];
+                placed = true;
+                break;
+            }
+            s = (s + 1) & cap_mask;
+        }
+        if (!placed) atomicOr(err, ST_TABLE_FULL);
+    }
 }
 
 template <int NW>
-__global__ void __launch_bounds__(256) mercy_scan_kernel(const uint32_t* __restrict__ packed,
-                                                         const uint64_t* __restrict__ frag_offs, uint64_t n_frags,
-                                                         int k, const Slot<NW>* __restrict__ table, uint64_t cap_mask,
-                                                         uint64_t* __restrict__ out, uint64_t out_cap,
-                                                         unsigned long long* __restrict__ counter) {
+__device__ __forceinline__ bool table_has(const Slot<NW>* __restrict__ table, uint64_t cap_mask, const Key<NW>& x) {
+    uint64_t h = key_hash<NW>(x);
+    uint32_t tag = slot_tag(h);
+    uint64_t s = h & cap_mask;
+    for (uint64_t probe = 0; probe <= cap_mask; probe++) {
+        uint32_t t = table[s].tag;
+        if (t == 0u) return false;
+        if (t == tag) {
+            bool eq = true;
+#pragma unroll
+            for (int w = 0; w < NW; w++) eq &= table[s].k[w] == x.w[w];
+            if (eq) return true;
+        }
+        s = (s + 1) & cap_mask;
+    }
+    return false;
+}
+
+// Probe every window; record windows without outdegree as (position, end).
+template <int NW>
+__global__ void __launch_bounds__(256) mercy_probe_kernel(const uint32_t* __restrict__ packed,
+                                                          const uint64_t* __restrict__ frag_offs, uint64_t n_frags,
+                                                          int k, const Slot<NW>* __restrict__ ends, uint64_t cap_mask,
+                                                          ulonglong2* __restrict__ hits, uint64_t hit_cap,
+                                                          unsigned long long* __restrict__ n_hits) {
     const int lane = threadIdx.x & 31;
-    const uint32_t lt_mask = (1u << lane) - 1;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const int K1 = k + 1;
@@ -114,46 +231,54 @@ __global__ void __launch_bounds__(256) mercy_scan_kernel(const uint32_t* __restr
         const uint64_t b = frag_offs[f];
         const uint64_t L = frag_offs[f + 1] - b;
         const uint64_t nwin = L > (uint64_t)k ? L - k : 0;
-        int64_t carry_pos = -1;
-        bool carry_out0 = false;
         for (uint64_t base = 0; base < nwin; base += 32) {
-            const uint64_t i = base + lane;
-            bool solid = false, o0 = false, i0 = false;
-            if (i < nwin) {
-                Key<NW> x = load_window<NW>(packed, b + i, K1);
-                Key<NW> r = key_rc<NW>(x, K1);
-                bool fwd_canon = !key_less<NW>(r, x);
-                int fl = table_find<NW>(table, cap_mask, fwd_canon ? x : r);
-                if (fl >= 0) {
-                    solid = true;
-                    // flags are stored for the canonical orientation; the
-                    // reverse orientation swaps outdegree and indegree
-                    o0 = fwd_canon ? (fl & 1) : ((fl >> 1) & 1);
-                    i0 = fwd_canon ? ((fl >> 1) & 1) : (fl & 1);
-                }
+            const uint64_t p = base + lane;
+            bool hit = false;
+            if (p < nwin) hit = (ends_find<NW>(ends, cap_mask, load_window<NW>(packed, b + p, K1)) & 1u) != 0;
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
+            if (!m) continue;
+            uint64_t first = 0;
+            if (lane == __ffs(m) - 1) first = atomicAdd(n_hits, (unsigned long long)__popc(m));
+            first = __shfl_sync(0xFFFFFFFFu, first, __ffs(m) - 1);
+            if (hit) {
+                uint64_t idx = first + __popc(m & ((1u << lane) - 1));
+                if (idx < hit_cap) hits[idx] = make_ulonglong2(b + p, b + nwin);
             }
-            const uint32_t mask = __ballot_sync(0xFFFFFFFFu, solid);
-            const uint32_t below = mask & lt_mask;
-            const int p_lane = below ? 31 - __clz(below) : 0;
-            const bool p_o0_lane = __shfl_sync(0xFFFFFFFFu, o0, p_lane);
-            int64_t p = below ? (int64_t)(base + p_lane) : carry_pos;
-            bool p_o0 = below ? p_o0_lane : carry_out0;
-            if (solid && p >= 0 && (int64_t)i > p + 1 && p_o0 && i0) {
-                uint64_t cnt = i - (uint64_t)p - 1;
-                uint64_t idx = atomicAdd(counter, (unsigned long long)cnt);
-                for (uint64_t j = (uint64_t)p + 1; j < i; j++, idx++) {
-                    if (idx >= out_cap) continue;
-                    Key<NW> y = load_window<NW>(packed, b + j, K1);
-                    Key<NW> ry = key_rc<NW>(y, K1);
-                    store_key<NW>(out, idx, key_less<NW>(ry, y) ? ry : y);
-                }
+        }
+    }
+}
+
+// Walk from each hit to the next solid window; emit the gap if it qualifies.
+template <int NW>
+__global__ void __launch_bounds__(256) mercy_walk_kernel(const uint32_t* __restrict__ packed,
+                                                         const ulonglong2* __restrict__ hits, uint64_t n_hits, int k,
+                                                         const Slot<NW>* __restrict__ ends, uint64_t ends_mask,
+                                                         const Slot<NW>* __restrict__ solid, uint64_t solid_mask,
+                                                         uint64_t* __restrict__ out, uint64_t out_cap,
+                                                         unsigned long long* __restrict__ counter) {
+    const int K1 = k + 1;
+    for (uint64_t h = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; h < n_hits;
+         h += (uint64_t)gridDim.x * blockDim.x) {
+        const ulonglong2 hp = hits[h];
+        const uint64_t p = hp.x, end = hp.y;
+        uint64_t q = p + 1;
+        Key<NW> y;
+        for (; q < end; q++) {
+            Key<NW> x = load_window<NW>(packed, q, K1);
+            Key<NW> r = key_rc<NW>(x, K1);
+            if (table_has<NW>(solid, solid_mask, key_less<NW>(r, x) ? r : x)) {
+                y = x;
+                break;
             }
-            if (mask) {
-                const int hl = 31 - __clz(mask);
-                const bool hl_o0 = __shfl_sync(0xFFFFFFFFu, o0, hl);
-                carry_pos = (int64_t)(base + hl);
-                carry_out0 = hl_o0;
-            }
+        }
+        if (q >= end || q == p + 1) continue;
+        if (!(ends_find<NW>(ends, ends_mask, y) & 2u)) continue;
+        uint64_t idx = atomicAdd(counter, (unsigned long long)(q - p - 1));
+        for (uint64_t j = p + 1; j < q; j++, idx++) {
+            if (idx >= out_cap) continue;
+            Key<NW> z = load_window<NW>(packed, j, K1);
+            Key<NW> rz = key_rc<NW>(z, K1);
+            store_key<NW>(out, idx, key_less<NW>(rz, z) ? rz : z);
         }
     }
 }
@@ -168,28 +293,60 @@ template <int NW>
 void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_kmers* out) {
     const int k = solid->k;
     const uint64_t S = solid->n;
-    const uint64_t cap = next_pow2(std::max<uint64_t>(2 * S, 64));
-    Buf<Slot<NW>> table(ctx, cap);
-    table.zero();
+    Buf<uint8_t> flags(ctx, S ? S : 1);
     Buf<uint64_t> stats(ctx, 2);
     stats.zero();
     if (S)
-        MH_LAUNCH(ctx, "degree_insert", grid_for(ctx, S, 256), 256, 0, degree_insert_kernel<NW>, solid->keys, S, k,
-                  table.p, cap - 1, (unsigned long long*)stats.p, ctx->d_status);
-    uint64_t out_cap = std::max<uint64_t>(1u << 20, reads->n_packed / 32);
+        MH_LAUNCH_B(ctx, "mercy_degree", S * 8 * NW, grid_for(ctx, ceil_div(S, kDegreeRun), 256), 256, 0,
+                    degree_kernel<NW>, solid->keys, S, k, flags.p, (unsigned long long*)stats.p);
+    uint64_t n_ends = 0;
+    read_u64(ctx, stats.p, &n_ends, 1);
+    const uint64_t cap = next_pow2(std::max<uint64_t>(2 * n_ends, 64));
+    Buf<Slot<NW>> table(ctx, cap);
+    table.zero();
+    if (n_ends)
+        MH_LAUNCH(ctx, "mercy_ends_insert", grid_for(ctx, S, 256), 256, 0, ends_insert_kernel<NW>, solid->keys, S,
+                  flags.p, table.p, cap - 1, ctx->d_status);
+    flags.reset();
+    // solidity set of the canonical solid keys, load <= 1/2 (<= 0.61 if all palindromes)
+    const uint64_t scap = next_pow2(std::max<uint64_t>(S + S / 2, 64));
+    Buf<Slot<NW>> sset(ctx, scap);
+    sset.zero();
+    if (S)
+        MH_LAUNCH(ctx, "mercy_solid_insert", grid_for(ctx, S, 256), 256, 0, solid_insert_kernel<NW>, solid->keys, S,
+                  k + 1, sset.p, scap - 1, ctx->d_status);
+    // windows without outdegree
+    uint64_t hit_cap = std::max<uint64_t>(1u << 20, reads->n_packed / 256);
+    Buf<ulonglong2> hits;
+    uint64_t n_hits = 0;
+    for (int attempt = 0; attempt < 2; attempt++) {
+        hits = Buf<ulonglong2>(ctx, hit_cap);
+        MH_CUDA(cudaMemsetAsync(stats.p + 1, 0, sizeof(uint64_t), ctx->stream));
+        if (reads->n_frags && n_ends)
+            MH_LAUNCH_B(ctx, "mercy_probe", reads->n_packed / 4, grid_for(ctx, reads->n_frags * 32, 256, 8), 256, 0,
+                        mercy_probe_kernel<NW>, reads->packed, reads->frag_offs, reads->n_frags, k, table.p, cap - 1,
+                        hits.p, hit_cap, (unsigned long long*)(stats.p + 1));
+        read_u64(ctx, stats.p + 1, &n_hits, 1);
+        if (n_hits <= hit_cap) break;
+        hit_cap = n_hits;
+    }
+    // the gaps behind the hits
+    uint64_t out_cap = std::max<uint64_t>(1u << 20, 4 * n_hits);
     Buf<uint64_t> cand;
     uint64_t n_cand = 0;
     for (int attempt = 0; attempt < 2; attempt++) {
         cand = Buf<uint64_t>(ctx, out_cap * NW);
         MH_CUDA(cudaMemsetAsync(stats.p + 1, 0, sizeof(uint64_t), ctx->stream));
-        if (reads->n_frags && S)
-            MH_LAUNCH(ctx, "mercy_scan", grid_for(ctx, reads->n_frags * 32, 256, 8), 256, 0, mercy_scan_kernel<NW>,
-                      reads->packed, reads->frag_offs, reads->n_frags, k, table.p, cap - 1, cand.p, out_cap,
+        if (n_hits)
+            MH_LAUNCH(ctx, "mercy_walk", grid_for(ctx, n_hits, 256, 8), 256, 0, mercy_walk_kernel<NW>, reads->packed,
+                      hits.p, n_hits, k, table.p, cap - 1, sset.p, scap - 1, cand.p, out_cap,
                       (unsigned long long*)(stats.p + 1));
         read_u64(ctx, stats.p + 1, &n_cand, 1);
         if (n_cand <= out_cap) break;
         out_cap = n_cand;
     }
+    hits.reset();
+    sset.reset();
     table.reset();
     Buf<uint64_t> alt(ctx, (n_cand ? n_cand : 1) * NW);
     bool in_alt = radix_sort<NW>(ctx, cand.p, alt.p, nullptr, nullptr, n_cand, 0, 2 * (k + 1));

@@ -30,11 +30,11 @@ static uint64_t chunk_tiles() {
     return v;
 }
 
-template <int NW, bool HV>
+template <int NW, bool HV, int ITEMS, int MINB>
 static bool radix_sort_impl(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt, uint64_t n,
                             int bit_lo, int bit_hi) {
     if (n <= 1 || bit_hi <= bit_lo) return false;
-    constexpr int TILE = sort_tile<NW>();
+    constexpr int TILE = sort_tile<NW, ITEMS>();
     const int n_passes = (bit_hi - bit_lo + 7) / 8;
     const uint64_t chunk_len = chunk_tiles() * TILE;
     const int n_chunks = (int)ceil_div(n, chunk_len);
@@ -48,8 +48,9 @@ static bool radix_sort_impl(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t
     const uint64_t max_tiles = std::min<uint64_t>(chunk_tiles(), ceil_div(n, TILE));
     Buf<uint32_t> status(ctx, max_tiles * 256);
     Buf<uint32_t> counter(ctx, 64);
-    constexpr size_t smem = onesweep_smem<NW, HV>();
-    MH_CUDA(cudaFuncSetAttribute(onesweep_kernel<NW, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    constexpr size_t smem = onesweep_smem<NW, HV, ITEMS>();
+    MH_CUDA(cudaFuncSetAttribute(onesweep_kernel<NW, HV, ITEMS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
     uint64_t *kin = keys, *kout = alt;
     uint32_t *vin = vals, *vout = valt;
     for (int p = 0; p < n_passes; p++) {
@@ -60,7 +61,7 @@ static bool radix_sort_impl(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t
             MH_CUDA(cudaMemsetAsync(status.p, 0, tiles * 256 * sizeof(uint32_t), ctx->stream));
             MH_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(uint32_t), ctx->stream));
             MH_LAUNCH_B(ctx, "radix_onesweep", len * (16 * NW + (HV ? 8 : 0)), (unsigned)tiles, kSortThreads, smem,
-                        (onesweep_kernel<NW, HV>), kin + c0 * NW, kout, HV ? vin + c0 : nullptr, vout, len,
+                        (onesweep_kernel<NW, HV, ITEMS, MINB>), kin + c0 * NW, kout, HV ? vin + c0 : nullptr, vout, len,
                         bit_lo + 8 * p, base.p + ((uint64_t)p * n_chunks + c) * 256,
                         c + 1 < n_chunks ? base.p + ((uint64_t)p * n_chunks + c + 1) * 256 : nullptr, status.p,
                         counter.p, ctx->d_status);
@@ -71,11 +72,35 @@ static bool radix_sort_impl(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t
     return (n_passes & 1) != 0;
 }
 
+// Tile shape of the scatter pass for 1-word keys: (items per thread,
+// resident CTAs per SM).  The default (12, 3) measured fastest on GB300;
+// MH_SORT_VARIANT selects another shape for tuning runs.
+static int sort_variant() {
+    static int v = [] {
+        const char* e = std::getenv("MH_SORT_VARIANT");
+        return e ? std::atoi(e) : 0;
+    }();
+    return v;
+}
+
+template <int NW, bool HV>
+static bool radix_sort_dispatch(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt,
+                                uint64_t n, int bit_lo, int bit_hi) {
+    if constexpr (NW == 1) {
+        switch (sort_variant()) {
+            case 1: return radix_sort_impl<NW, HV, 16, 2>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
+            case 2: return radix_sort_impl<NW, HV, 8, 4>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
+            default: return radix_sort_impl<NW, HV, 12, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
+        }
+    }
+    return radix_sort_impl<NW, HV, SortItems<NW>::v, 2>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
+}
+
 template <int NW>
 bool radix_sort(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt, uint64_t n, int bit_lo,
                 int bit_hi) {
-    if (vals) return radix_sort_impl<NW, true>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
-    return radix_sort_impl<NW, false>(ctx, keys, alt, nullptr, nullptr, n, bit_lo, bit_hi);
+    if (vals) return radix_sort_dispatch<NW, true>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
+    return radix_sort_dispatch<NW, false>(ctx, keys, alt, nullptr, nullptr, n, bit_lo, bit_hi);
 }
 
 template bool radix_sort<1>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*, uint64_t, int, int);

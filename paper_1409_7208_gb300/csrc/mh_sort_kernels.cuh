@@ -29,15 +29,15 @@ struct SortItems<4> {
     static constexpr int v = 6;
 };
 
-template <int NW>
+template <int NW, int ITEMS = SortItems<NW>::v>
 __host__ __device__ constexpr int sort_tile() {
-    return kSortThreads * SortItems<NW>::v;
+    return kSortThreads * ITEMS;
 }
 
-template <int NW, bool HV>
+template <int NW, bool HV, int ITEMS = SortItems<NW>::v>
 constexpr size_t onesweep_smem() {
     return sizeof(uint32_t) * (kSortWarps * 256 + 256 + 256 + 8) + sizeof(uint64_t) * 256 +
-           sizeof(uint64_t) * NW * sort_tile<NW>() + (HV ? sizeof(uint32_t) * sort_tile<NW>() : 0);
+           sizeof(uint64_t) * NW * sort_tile<NW, ITEMS>() + (HV ? sizeof(uint32_t) * sort_tile<NW, ITEMS>() : 0);
 }
 
 // ------------------------------------------------------------ histogram
@@ -78,19 +78,16 @@ static __global__ void radix_base_kernel(const uint32_t* __restrict__ hist, uint
 }
 
 // --------------------------------------------------------------- onesweep
-template <int NW, bool HV>
-__global__ void __launch_bounds__(kSortThreads, 2)
+template <int NW, bool HV, int ITEMS = SortItems<NW>::v, int MINB = 2>
+__global__ void __launch_bounds__(kSortThreads, MINB)
     onesweep_kernel(const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout, const uint32_t* __restrict__ vin,
                     uint32_t* __restrict__ vout, uint64_t n, int shift, const uint64_t* __restrict__ digit_base,
                     uint64_t* __restrict__ next_base, uint32_t* __restrict__ status,
                     uint32_t* __restrict__ tile_counter, uint32_t* __restrict__ err) {
-    constexpr int ITEMS = SortItems<NW>::v;
-    constexpr int TILE = sort_tile<NW>();
+    constexpr int TILE = sort_tile<NW, ITEMS>();
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* warp_hist = reinterpret_cast<uint32_t*>(smem);          // [warps][256]
-    uint32_t* tile_cnt = warp_hist + kSortWarps * 256;                 // [256]
-    uint32_t* tile_start = tile_cnt + 256;                             // [256]
-    uint32_t* misc = tile_start + 256;                                 // [8]
+    uint32_t* misc = warp_hist + kSortWarps * 256 + 512;               // [8]
     uint64_t* scatter_base = reinterpret_cast<uint64_t*>(misc + 8);    // [256]
     uint64_t* stage = scatter_base + 256;                              // [NW][TILE]
     uint32_t* vstage = reinterpret_cast<uint32_t*>(stage + NW * TILE); // [TILE]
@@ -101,40 +98,50 @@ __global__ void __launch_bounds__(kSortThreads, 2)
     __syncthreads();
     const uint32_t tile = misc[0];
     const uint64_t tile_base = (uint64_t)tile * TILE;
+    const uint64_t rem = n - tile_base;
+    const uint32_t tile_n = rem < (uint64_t)TILE ? (uint32_t)rem : (uint32_t)TILE;
+    const bool full = tile_n == (uint32_t)TILE;
+    const uint64_t* kt = kin + tile_base * NW;
+    const uint32_t* vt = HV ? vin + tile_base : nullptr;
 
-    // load: warp-striped, item i of lane l is key tile_base + warp*32*ITEMS + 32*i + l
+    // load: warp-striped, item i of lane l is tile key warp*32*ITEMS + 32*i + l
     Key<NW> k[ITEMS];
     uint32_t v[HV ? ITEMS : 1];
-    uint32_t rank[ITEMS];
-    const uint64_t wbase = tile_base + (uint64_t)warp * 32 * ITEMS;
+    uint32_t rd[ITEMS];  // (rank within warp << 8) | digit
+    const uint32_t w0 = (uint32_t)warp * 32 * ITEMS + lane;
+    if (full) {
 #pragma unroll
-    for (int i = 0; i < ITEMS; i++) {
-        uint64_t idx = wbase + 32 * i + lane;
-        if (idx < n) {
-            k[i] = load_key<NW>(kin, idx);
-            if constexpr (HV) v[i] = vin[idx];
-        } else {
+        for (int i = 0; i < ITEMS; i++) {
+            k[i] = load_key<NW>(kt, w0 + 32 * i);
+            if constexpr (HV) v[i] = vt[w0 + 32 * i];
+        }
+    } else {
 #pragma unroll
-            for (int w = 0; w < NW; w++) k[i].w[w] = 0;
-            if constexpr (HV) v[i] = 0;
+        for (int i = 0; i < ITEMS; i++) {
+            if (w0 + 32 * i < tile_n) {
+                k[i] = load_key<NW>(kt, w0 + 32 * i);
+                if constexpr (HV) v[i] = vt[w0 + 32 * i];
+            } else {
+#pragma unroll
+                for (int w = 0; w < NW; w++) k[i].w[w] = 0;
+                if constexpr (HV) v[i] = 0;
+            }
         }
     }
-    // rank within the warp, stable by item then lane
+    // rank within the warp, stable by item then lane: the first lane of each
+    // group of equal digits adds the group size to the warp's counter
     uint32_t* wh = warp_hist + warp * 256;
     const uint32_t lt_mask = (1u << lane) - 1;
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
-        uint64_t idx = wbase + 32 * i + lane;
-        uint32_t dg = idx < n ? key_digit<NW>(k[i], shift) : 256u;
-        uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg);
-        int leader = __ffs(peers) - 1;
+        const bool valid = full || (w0 + 32 * i < tile_n);
+        const uint32_t dg = valid ? key_digit<NW>(k[i], shift) : 256u;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg);
+        const int leader = __ffs(peers) - 1;
         uint32_t old = 0;
-        if (lane == leader && dg < 256u) {
-            old = wh[dg];
-            wh[dg] = old + __popc(peers);
-        }
+        if (lane == leader && valid) old = atomicAdd(&wh[dg], (uint32_t)__popc(peers));
         old = __shfl_sync(0xFFFFFFFFu, old, leader);
-        rank[i] = old + __popc(peers & lt_mask);
+        rd[i] = ((old + __popc(peers & lt_mask)) << 8) | (dg & 0xFFu);
         __syncwarp();
     }
     __syncthreads();
@@ -147,11 +154,11 @@ __global__ void __launch_bounds__(kSortThreads, 2)
         warp_hist[w * 256 + d] = cnt;
         cnt += c;
     }
-    tile_cnt[d] = cnt;
     // publish this tile's count early so later tiles can proceed
     uint32_t* st = status + (uint64_t)tile * 256 + d;
     st_relaxed_u32(st, (tile == 0 ? kFlagInc : kFlagAgg) | cnt);
-    // block exclusive scan of tile_cnt -> tile_start
+    // block exclusive scan of the tile counts -> start of digit d in the tile
+    uint32_t start;
     {
         uint32_t x = cnt;
 #pragma unroll
@@ -162,9 +169,13 @@ __global__ void __launch_bounds__(kSortThreads, 2)
         if (lane == 31) misc[warp] = x;  // misc[0..7]; misc[0] (tile) already read
         __syncthreads();
         uint32_t wpre = 0;
-        for (int w = 0; w < warp; w++) wpre += misc[w];
-        tile_start[d] = wpre + x - cnt;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; w++) wpre += w < warp ? misc[w] : 0u;
+        start = wpre + x - cnt;
     }
+    // staging offset of digit d for each warp
+#pragma unroll
+    for (int w = 0; w < kSortWarps; w++) warp_hist[w * 256 + d] += start;
     // look back over earlier tiles for this digit
     uint64_t excl = 0;
     if (tile > 0) {
@@ -190,33 +201,33 @@ __global__ void __launch_bounds__(kSortThreads, 2)
         if (!ok) atomicOr(err, ST_SPIN_TIMEOUT);
         st_relaxed_u32(st, kFlagInc | (uint32_t)((excl + cnt) & kCountMask));
     }
-    scatter_base[d] = digit_base[d] + excl - tile_start[d];
+    scatter_base[d] = digit_base[d] + excl - start;
     // the chunk's last tile: where the next chunk starts writing digit d
     if (next_base && (uint64_t)(tile + 1) * TILE >= n) next_base[d] = digit_base[d] + excl + cnt;
     __syncthreads();
     // stage in tile digit order
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
-        uint64_t idx = wbase + 32 * i + lane;
-        if (idx < n) {
-            uint32_t dg = key_digit<NW>(k[i], shift);
-            uint32_t pos = tile_start[dg] + warp_hist[warp * 256 + dg] + rank[i];
+        if (full || (w0 + 32 * i < tile_n)) {
+            const uint32_t pos = wh[rd[i] & 0xFFu] + (rd[i] >> 8);
 #pragma unroll
             for (int w = 0; w < NW; w++) stage[w * TILE + pos] = k[i].w[w];
             if constexpr (HV) vstage[pos] = v[i];
         }
     }
     __syncthreads();
-    const uint64_t rem = n - tile_base;
-    const int n_valid = rem < (uint64_t)TILE ? (int)rem : TILE;
-    for (int j = tid; j < n_valid; j += kSortThreads) {
-        Key<NW> kk;
+    // write out: consecutive staged keys of one digit go to consecutive addresses
 #pragma unroll
-        for (int w = 0; w < NW; w++) kk.w[w] = stage[w * TILE + j];
-        uint32_t dg = key_digit<NW>(kk, shift);
-        uint64_t dst = scatter_base[dg] + j;
-        store_key<NW>(kout, dst, kk);
-        if constexpr (HV) vout[dst] = vstage[j];
+    for (int i = 0; i < ITEMS; i++) {
+        const uint32_t j = tid + i * kSortThreads;
+        if (full || j < tile_n) {
+            Key<NW> kk;
+#pragma unroll
+            for (int w = 0; w < NW; w++) kk.w[w] = stage[w * TILE + j];
+            const uint64_t dst = scatter_base[key_digit<NW>(kk, shift)] + j;
+            store_key<NW>(kout, dst, kk);
+            if constexpr (HV) vout[dst] = vstage[j];
+        }
     }
 }
 
