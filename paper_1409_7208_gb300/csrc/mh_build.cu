@@ -11,8 +11,9 @@
 //   targets   A = reversed targets (label, e[k-1], ..., e[1]) of unflagged
 //             entries; already ascending within each label, so one stable
 //             radix pass on their top 8 bits sorts them
-//   joins     zero indegree = B \ A, zero outdegree = A \ B (binary searches of
-//             sorted queries in sorted arrays)
+//   joins     zero indegree = B \ A, zero outdegree = A \ B (sorted queries
+//             in sorted arrays: each thread gallops through 16 consecutive
+//             queries)
 //   padding   dummy entries (node $ v[0..k-2], label v[k-1]) sorted by
 //             (v[k-2..0], v[k-1]); $ entries in the order of A \ B
 //   merge     final position of every entry: its rank in its own list plus
@@ -64,16 +65,6 @@ __device__ __forceinline__ uint64_t lb_ext(const uint64_t* __restrict__ a, uint6
         else if (KIND == 1) ext_of_dummy<NW>(x, gx, tx);
         else ext_of_dollar<NW>(x, gx, tx);
         if (ext_less<NW>(gx, tx, g, t)) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-template <int NW>
-__device__ __forceinline__ uint64_t lower_bound_plain(const uint64_t* __restrict__ a, uint64_t n, const Key<NW>& q) {
-    uint64_t lo = 0, hi = n;
-    while (lo < hi) {
-        uint64_t mid = (lo + hi) >> 1;
-        if (key_less<NW>(load_key<NW>(a, mid), q)) lo = mid + 1; else hi = mid;
     }
     return lo;
 }
@@ -140,14 +131,23 @@ __global__ void select_nodes_targets_kernel(const uint64_t* __restrict__ ck, uin
     }
 }
 
-// flag[i] = 1 iff q[i] is absent from the sorted array a.
+// flag[i] = 1 iff q[i] is absent from the sorted array a.  The queries are
+// sorted too: each thread takes 16 consecutive ones and gallops from the
+// previous answer.
+constexpr int kAbsentRun = 16;
 template <int NW>
 __global__ void absent_kernel(const uint64_t* __restrict__ q, uint64_t nq, const uint64_t* __restrict__ a, uint64_t na,
                               uint32_t* __restrict__ flag) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nq; i += (uint64_t)gridDim.x * blockDim.x) {
-        Key<NW> x = load_key<NW>(q, i);
-        uint64_t lb = lower_bound_plain<NW>(a, na, x);
-        flag[i] = !(lb < na && key_eq<NW>(load_key<NW>(a, lb), x));
+    for (uint64_t i0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) * kAbsentRun; i0 < nq;
+         i0 += (uint64_t)gridDim.x * blockDim.x * kAbsentRun) {
+        uint64_t hint = na / 2;
+        const uint64_t i1 = i0 + kAbsentRun < nq ? i0 + kAbsentRun : nq;
+        for (uint64_t i = i0; i < i1; i++) {
+            Key<NW> x = load_key<NW>(q, i);
+            uint64_t lb = gallop_lb<NW>(a, na, x, hint);
+            hint = lb;
+            flag[i] = !(lb < na && key_eq<NW>(load_key<NW>(a, lb), x));
+        }
     }
 }
 
@@ -329,9 +329,11 @@ void build_sdbg(mh_ctx* ctx, const mh_kmers* solid, const mh_kmers* mercy, mh_sd
     // zero indegree: B \ A; zero outdegree: A \ B
     Buf<uint32_t> zf_b(ctx, nB ? nB : 1), zf_a(ctx, nA ? nA : 1);
     if (nB)
-        MH_LAUNCH(ctx, "absent_nodes", grid_for(ctx, nB, 256), 256, 0, absent_kernel<NW>, B.p, nB, A.p, nA, zf_b.p);
+        MH_LAUNCH(ctx, "absent_nodes", grid_for(ctx, ceil_div(nB, kAbsentRun), 256), 256, 0, absent_kernel<NW>, B.p, nB,
+                  A.p, nA, zf_b.p);
     if (nA)
-        MH_LAUNCH(ctx, "absent_targets", grid_for(ctx, nA, 256), 256, 0, absent_kernel<NW>, A.p, nA, B.p, nB, zf_a.p);
+        MH_LAUNCH(ctx, "absent_targets", grid_for(ctx, ceil_div(nA, kAbsentRun), 256), 256, 0, absent_kernel<NW>, A.p,
+                  nA, B.p, nB, zf_a.p);
     Buf<uint64_t> pz_b, pz_a;
     const uint64_t t = flag_positions(ctx, zf_b.p, nB, pz_b);
     const uint64_t u = flag_positions(ctx, zf_a.p, nA, pz_a);

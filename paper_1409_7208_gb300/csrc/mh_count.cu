@@ -9,7 +9,8 @@
 //
 //   extract   warp per fragment, window keys from the packed words, canonical
 //   sort      LSD radix over the 2(k+1) key bits
-//   runs      run heads, run lengths by galloping search, solid filter
+//   runs      run heads in a shared-memory bitmask, run lengths from the
+//             next head, solid filter, outputs placed by decoupled look-back
 //   expand    each solid canonical key -> itself and its reverse complement
 //   sort      key-value LSD radix -> solid table in ascending key order
 #include "mh_internal.cuh"
@@ -47,172 +48,263 @@ __global__ void __launch_bounds__(256) extract_canonical_kernel(const uint32_t* 
     }
 }
 
-constexpr int kRunThreads = 256;
-constexpr int kRunItems = 8;
-constexpr int kRunTile = kRunThreads * kRunItems;
+// ---------------------------------------------------------------- runs
+// Run-length counting of a sorted key array in one read: a tile of keys is
+// loaded to shared memory, run heads (key differs from its predecessor) are
+// marked in a bitmask, each run's end is the next head (in the tile, or the
+// first head of a later tile for the tile's last run), and the kept runs'
+// outputs are placed with a decoupled look-back over per-tile output counts.
 
-// First index j > i with s[j] != s[i] (or n), by galloping then bisection.
+constexpr int kRunThreads = 256;
+constexpr int kRunItems = 16;
+constexpr int kRunTile = kRunThreads * kRunItems;  // keys per tile
+constexpr int kRunTilePad = kRunTile + kRunTile / 16;
+__device__ __forceinline__ uint32_t rp(uint32_t i) { return i + (i >> 4); }
+constexpr uint64_t kNoHead = ~0ull;
+constexpr uint64_t kRunAgg = 1ull << 62;
+constexpr uint64_t kRunInc = 2ull << 62;
+constexpr uint64_t kRunCountMask = (1ull << 62) - 1;
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// first[t] = index of the first run head in tile t, or kNoHead (warp per tile).
 template <int NW>
-__device__ __forceinline__ uint64_t run_end(const uint64_t* __restrict__ s, uint64_t n, uint64_t i,
-                                            const Key<NW>& x) {
-    uint64_t step = 1, lo = i;  // s[lo] == x
-    while (true) {
-        uint64_t j = i + step;
-        if (j >= n) {
-            j = n;
-            // bisection on (lo, n]
-            uint64_t hi = n;
-            while (hi - lo > 1) {
-                uint64_t mid = lo + (hi - lo) / 2;
-                if (key_eq<NW>(load_key<NW>(s, mid), x)) lo = mid; else hi = mid;
+__global__ void run_first_head_kernel(const uint64_t* __restrict__ s, uint64_t n, uint64_t n_tiles,
+                                      uint64_t* __restrict__ first) {
+    const int lane = threadIdx.x & 31;
+    for (uint64_t t = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; t < n_tiles;
+         t += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
+        const uint64_t start = t * kRunTile, end = start + kRunTile < n ? start + kRunTile : n;
+        uint64_t f = kNoHead;
+        for (uint64_t base = start; base < end; base += 32) {
+            const uint64_t i = base + lane;
+            bool head = false;
+            if (i < end) head = i == 0 || !key_eq<NW>(load_key<NW>(s, i), load_key<NW>(s, i - 1));
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, head);
+            if (m) {
+                f = base + __ffs(m) - 1;
+                break;
             }
-            return hi;
         }
-        if (!key_eq<NW>(load_key<NW>(s, j), x)) {
-            uint64_t hi = j;
-            while (hi - lo > 1) {
-                uint64_t mid = lo + (hi - lo) / 2;
-                if (key_eq<NW>(load_key<NW>(s, mid), x)) lo = mid; else hi = mid;
-            }
-            return hi;
-        }
-        lo = j;
-        step <<= 1;
+        if (lane == 0) first[t] = f;
     }
 }
 
-// What a run contributes.  mode 0 (counting): literal count = len (x2 for a
-// palindrome); kept if >= d; outputs 1 (palindrome) or 2 keys.  mode 1
-// (dedup with counts from a spectrum): every run kept, count looked up.
-struct RunOut {
-    uint32_t n_out;
-    uint32_t count;
-    bool palin;
-};
+// next[t] = first head after tile t (in tiles t+1, t+2, ...), or n.
+__global__ void run_next_head_kernel(const uint64_t* __restrict__ first, uint64_t n_tiles, uint64_t n,
+                                     uint64_t* __restrict__ next) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n_tiles;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t u = t + 1;
+        while (u < n_tiles && first[u] == kNoHead) u++;
+        next[t] = u < n_tiles ? first[u] : n;
+    }
+}
 
 template <int NW>
 __device__ __forceinline__ uint64_t spectrum_count(const uint64_t* __restrict__ spec, uint64_t n_spec,
                                                    const Key<NW>& x) {
-    // lower bound
     uint64_t lo = 0, hi = n_spec;
     while (lo < hi) {
         uint64_t mid = (lo + hi) >> 1;
         if (key_less<NW>(load_key<NW>(spec, mid), x)) lo = mid + 1; else hi = mid;
     }
-    if (lo >= n_spec || !key_eq<NW>(load_key<NW>(spec, lo), x)) return 0;
-    return run_end<NW>(spec, n_spec, lo, x) - lo;
-}
-
-template <int NW>
-__device__ __forceinline__ RunOut run_info(const uint64_t* __restrict__ s, uint64_t n, uint64_t i, const Key<NW>& x,
-                                           int K1, int d, const uint64_t* __restrict__ spec, uint64_t n_spec,
-                                           uint32_t* __restrict__ err) {
-    Key<NW> r = key_rc<NW>(x, K1);
-    bool palin = key_eq<NW>(r, x);
-    uint64_t len = spec ? spectrum_count<NW>(spec, n_spec, x) : run_end<NW>(s, n, i, x) - i;
-    uint64_t c = palin ? 2 * len : len;
-    if (c > 0xFFFFFFFFull) {
-        atomicOr(err, ST_OVERFLOW);
-        c = 0xFFFFFFFFull;
+    const uint64_t first = lo;
+    hi = n_spec;
+    while (lo < hi) {
+        uint64_t mid = (lo + hi) >> 1;
+        if (key_less<NW>(x, load_key<NW>(spec, mid))) hi = mid; else lo = mid + 1;
     }
-    RunOut o;
-    o.palin = palin;
-    o.count = (uint32_t)c;
-    o.n_out = (spec || c >= (uint64_t)d) ? (palin ? 1u : 2u) : 0u;
-    return o;
+    return lo - first;
 }
 
-// Pass 1: per tile, the number of output keys; also distinct-run totals.
+// Counting mode (spec == nullptr): a run of length len is the canonical key
+// of len windows; its literal count is len, doubled for a palindrome; it is
+// kept if the count is >= d.  Lookup mode: every run is kept and its count
+// is looked up in the spectrum.  A kept run outputs the key and, unless it is
+// a palindrome, its reverse complement, both with the count.
 template <int NW>
-__global__ void __launch_bounds__(kRunThreads) runs_count_kernel(const uint64_t* __restrict__ s, uint64_t n, int K1,
-                                                                 int d, const uint64_t* __restrict__ spec,
-                                                                 uint64_t n_spec, uint64_t* __restrict__ tile_out,
-                                                                 unsigned long long* __restrict__ totals,
-                                                                 uint32_t* __restrict__ err) {
-    uint64_t t0 = (uint64_t)blockIdx.x * kRunTile;
-    uint32_t outs = 0, heads = 0, palins = 0;
+__global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __restrict__ s, uint64_t n, int K1, int d,
+                                                           const uint64_t* __restrict__ spec, uint64_t n_spec,
+                                                           const uint64_t* __restrict__ next_head,
+                                                           uint64_t* __restrict__ out_keys,
+                                                           uint32_t* __restrict__ out_cnt, uint64_t out_cap,
+                                                           uint64_t* __restrict__ status,
+                                                           uint32_t* __restrict__ tile_counter,
+                                                           unsigned long long* __restrict__ totals,
+                                                           uint32_t* __restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    // tile keys, one pad key after every 16 so that threads reading 16
+    // consecutive keys each hit distinct banks: key i at tk[rp(i) * NW]
+    uint64_t* tk = reinterpret_cast<uint64_t*>(smem);                          // [(TILE + TILE/16) * NW]
+    uint32_t* head_bits = reinterpret_cast<uint32_t*>(tk + kRunTilePad * NW);  // [TILE / 32]
+    uint32_t* wsum = head_bits + kRunTile / 32;                              // [8]
+    uint64_t* tile_off = reinterpret_cast<uint64_t*>(wsum + 8);             // [1]
+    uint32_t* tile_id = reinterpret_cast<uint32_t*>(tile_off + 1);          // [1]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) *tile_id = atomicAdd(tile_counter, 1u);
+    __syncthreads();
+    const uint64_t tile = *tile_id;
+    const uint64_t start = tile * kRunTile;
+    const uint32_t tn = (uint32_t)(n - start < (uint64_t)kRunTile ? n - start : (uint64_t)kRunTile);
+    for (uint32_t i = tid; i < tn; i += kRunThreads) {
+        Key<NW> x = load_key<NW>(s, start + i);
 #pragma unroll
-    for (int it = 0; it < kRunItems; it++) {
-        uint64_t i = t0 + it * kRunThreads + threadIdx.x;
-        if (i >= n) break;
-        Key<NW> x = load_key<NW>(s, i);
-        if (i > 0 && key_eq<NW>(load_key<NW>(s, i - 1), x)) continue;
-        RunOut o = run_info<NW>(s, n, i, x, K1, d, spec, n_spec, err);
-        outs += o.n_out;
-        heads++;
-        palins += o.palin;
-    }
-    __shared__ uint32_t red[3][kRunThreads / 32];
-    for (int off = 16; off; off >>= 1) {
-        outs += __shfl_xor_sync(0xFFFFFFFFu, outs, off);
-        heads += __shfl_xor_sync(0xFFFFFFFFu, heads, off);
-        palins += __shfl_xor_sync(0xFFFFFFFFu, palins, off);
-    }
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        red[0][warp] = outs;
-        red[1][warp] = heads;
-        red[2][warp] = palins;
+        for (int w = 0; w < NW; w++) tk[rp(i) * NW + w] = x.w[w];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        uint64_t a = 0, b = 0, c = 0;
-        for (int w = 0; w < kRunThreads / 32; w++) {
-            a += red[0][w];
-            b += red[1][w];
-            c += red[2][w];
-        }
-        tile_out[blockIdx.x] = a;
-        atomicAdd(&totals[0], (unsigned long long)b);
-        atomicAdd(&totals[1], (unsigned long long)c);
-    }
-}
-
-// Pass 2: write the kept runs' keys (and reverse complements) with counts.
-template <int NW>
-__global__ void __launch_bounds__(kRunThreads) runs_write_kernel(const uint64_t* __restrict__ s, uint64_t n, int K1,
-                                                                 int d, const uint64_t* __restrict__ spec,
-                                                                 uint64_t n_spec, const uint64_t* __restrict__ tile_off,
-                                                                 uint64_t* __restrict__ keys, uint32_t* __restrict__ cnt,
-                                                                 uint32_t* __restrict__ err) {
-    uint64_t t0 = (uint64_t)blockIdx.x * kRunTile;
-    uint32_t mine = 0;
-    RunOut o[kRunItems];
-    Key<NW> xs[kRunItems];
+    // head bitmask, one warp per 32-key word
+    for (uint32_t wd = warp; wd < kRunTile / 32; wd += kRunThreads / 32) {
+        const uint32_t i = wd * 32 + lane;
+        bool head = false;
+        if (i < tn) {
+            Key<NW> x, y;
 #pragma unroll
-    for (int it = 0; it < kRunItems; it++) {
-        o[it].n_out = 0;
-        uint64_t i = t0 + it * kRunThreads + threadIdx.x;
-        if (i >= n) continue;
-        xs[it] = load_key<NW>(s, i);
-        if (i > 0 && key_eq<NW>(load_key<NW>(s, i - 1), xs[it])) continue;
-        o[it] = run_info<NW>(s, n, i, xs[it], K1, d, spec, n_spec, err);
-        mine += o[it].n_out;
+            for (int w = 0; w < NW; w++) x.w[w] = tk[rp(i) * NW + w];
+            if (i > 0) {
+#pragma unroll
+                for (int w = 0; w < NW; w++) y.w[w] = tk[rp(i - 1) * NW + w];
+            } else {
+                y = start > 0 ? load_key<NW>(s, start - 1) : x;
+            }
+            head = (start + i == 0) || !key_eq<NW>(x, y);
+        }
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, head);
+        if (lane == 0) head_bits[wd] = m;
     }
-    // block exclusive scan of per-thread output counts (thread order)
-    __shared__ uint32_t ws[kRunThreads / 32];
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = mine;
+    __syncthreads();
+    // each thread: kRunItems consecutive keys
+    const uint32_t i0 = tid * kRunItems;
+    uint32_t outs = 0, heads = 0, palins = 0;
+    uint32_t hmask = i0 < tn ? (head_bits[i0 >> 5] >> (i0 & 31)) & 0xFFFFu : 0u;  // kRunItems == 16
+    uint32_t cnt[kRunItems];
+    uint8_t nout[kRunItems];
+#pragma unroll
+    for (int j = 0; j < kRunItems; j++) {
+        nout[j] = 0;
+        cnt[j] = 0;
+        if (!((hmask >> j) & 1u)) continue;
+        const uint32_t i = i0 + j;
+        // next head after i in this tile
+        uint64_t end = kNoHead;
+        uint32_t wd = i >> 5;
+        uint32_t m = head_bits[wd] & ~((2u << (i & 31)) - 1u);
+        while (true) {
+            if (m) {
+                end = start + wd * 32 + (uint32_t)(__ffs(m) - 1);
+                break;
+            }
+            if (++wd >= (tn + 31) / 32) break;
+            m = head_bits[wd];
+        }
+        if (end == kNoHead || end > start + tn) end = next_head[tile];
+        Key<NW> x;
+#pragma unroll
+        for (int w = 0; w < NW; w++) x.w[w] = tk[rp(i) * NW + w];
+        const bool palin = key_eq<NW>(key_rc<NW>(x, K1), x);
+        const uint64_t len = spec ? spectrum_count<NW>(spec, n_spec, x) : end - (start + i);
+        uint64_t c = palin ? 2 * len : len;
+        if (c > 0xFFFFFFFFull) {
+            atomicOr(err, ST_OVERFLOW);
+            c = 0xFFFFFFFFull;
+        }
+        cnt[j] = (uint32_t)c;
+        if (spec || c >= (uint64_t)d) nout[j] = palin ? 1 : 2;
+        outs += nout[j];
+        heads++;
+        palins += palin;
+    }
+    // block exclusive scan of outs
+    uint32_t x = outs;
+#pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
         if (lane >= off) x += y;
     }
-    if (lane == 31) ws[warp] = x;
+    if (lane == 31) wsum[warp] = x;
     __syncthreads();
-    uint32_t pre = 0;
-    for (int w = 0; w < warp; w++) pre += ws[w];
-    uint64_t pos = tile_off[blockIdx.x] + pre + x - mine;
+    uint32_t wpre = 0, total = 0;
 #pragma unroll
-    for (int it = 0; it < kRunItems; it++) {
-        if (!o[it].n_out) continue;
-        store_key<NW>(keys, pos, xs[it]);
-        cnt[pos] = o[it].count;
+    for (int w = 0; w < kRunThreads / 32; w++) {
+        wpre += w < warp ? wsum[w] : 0u;
+        total += wsum[w];
+    }
+    const uint32_t excl_thread = wpre + x - outs;
+    if (tid == 0) {
+        uint64_t* st = status + tile;
+        st_relaxed_u64(st, (tile == 0 ? kRunInc : kRunAgg) | total);
+        uint64_t excl = 0;
+        if (tile > 0) {
+            int64_t j = (int64_t)tile - 1;
+            bool ok = true;
+            while (j >= 0) {
+                uint64_t v = ld_relaxed_u64(status + j);
+                int spins = 0;
+                while ((v & ~kRunCountMask) == 0) {
+                    if (++spins > (1 << 23)) {
+                        ok = false;
+                        break;
+                    }
+                    if (spins > 64) __nanosleep(128);
+                    v = ld_relaxed_u64(status + j);
+                }
+                if (!ok) break;
+                excl += v & kRunCountMask;
+                if ((v & ~kRunCountMask) == kRunInc) break;
+                j--;
+            }
+            if (!ok) atomicOr(err, ST_SPIN_TIMEOUT);
+            st_relaxed_u64(st, kRunInc | (excl + total));
+        }
+        *tile_off = excl;
+    }
+    // per-tile totals of runs and palindromic runs
+    uint32_t hs = heads, ps = palins;
+    for (int off = 16; off; off >>= 1) {
+        hs += __shfl_xor_sync(0xFFFFFFFFu, hs, off);
+        ps += __shfl_xor_sync(0xFFFFFFFFu, ps, off);
+    }
+    if (lane == 0 && (hs || ps)) {
+        atomicAdd(&totals[0], (unsigned long long)hs);
+        atomicAdd(&totals[1], (unsigned long long)ps);
+    }
+    __syncthreads();
+    uint64_t pos = *tile_off + excl_thread;
+    if (pos + outs > out_cap) {
+        if (outs) atomicOr(err, ST_TABLE_FULL);
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < kRunItems; j++) {
+        if (!nout[j]) continue;
+        const uint32_t i = i0 + j;
+        Key<NW> xk;
+#pragma unroll
+        for (int w = 0; w < NW; w++) xk.w[w] = tk[rp(i) * NW + w];
+        store_key<NW>(out_keys, pos, xk);
+        out_cnt[pos] = cnt[j];
         pos++;
-        if (o[it].n_out == 2) {
-            store_key<NW>(keys, pos, key_rc<NW>(xs[it], K1));
-            cnt[pos] = o[it].count;
+        if (nout[j] == 2) {
+            store_key<NW>(out_keys, pos, key_rc<NW>(xk, K1));
+            out_cnt[pos] = cnt[j];
             pos++;
         }
+    }
+}
+
+template <int NW>
+__global__ void copy_keys_counts_kernel(const uint64_t* __restrict__ k, const uint32_t* __restrict__ c, uint64_t n,
+                                        uint64_t* __restrict__ k2, uint32_t* __restrict__ c2) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        store_key<NW>(k2, i, load_key<NW>(k, i));
+        c2[i] = c[i];
     }
 }
 
@@ -225,26 +317,45 @@ void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, 
                  const uint64_t* spectrum, uint64_t n_spectrum) {
     const int K1 = k + 1;
     const uint64_t tiles = ceil_div(n ? n : 1, kRunTile);
-    Buf<uint64_t> tile_out(ctx, tiles + 1), tile_off(ctx, tiles + 1);
-    Buf<uint64_t> totals(ctx, 2);
+    // outputs: <= n when every kept run has >= 2 keys or is a palindrome (d >= 2), else <= 2n
+    const uint64_t cap = std::max<uint64_t>(1, (!spectrum && d >= 2) ? n : 2 * n);
+    Buf<uint64_t> first(ctx, tiles), next(ctx, tiles), status(ctx, tiles), totals(ctx, 2);
+    Buf<uint32_t> counter(ctx, 1);
+    Buf<uint64_t> big_k(ctx, cap * NW);
+    Buf<uint32_t> big_c(ctx, cap);
     totals.zero();
-    tile_out.zero();
-    if (n)
-        MH_LAUNCH_B(ctx, "runs_count", n * 8 * NW, (unsigned)tiles, kRunThreads, 0, runs_count_kernel<NW>, sorted, n, K1,
-                    d, spectrum, n_spectrum, tile_out.p, (unsigned long long*)totals.p, ctx->d_status);
-    exclusive_scan_u64(ctx, tile_out.p, tile_off.p, tiles);
-    uint64_t tot[3];
-    read_u64(ctx, tile_off.p + tiles, &tot[0], 1);
-    read_u64(ctx, totals.p, &tot[1], 2);
-    const uint64_t S = tot[0];
+    uint64_t S = 0, tot[2] = {0, 0};
+    if (n) {
+        status.zero();
+        counter.zero();
+        MH_LAUNCH(ctx, "runs_first_head", grid_for(ctx, tiles * 32, 256), 256, 0, run_first_head_kernel<NW>, sorted, n,
+                  tiles, first.p);
+        MH_LAUNCH(ctx, "runs_next_head", grid_for(ctx, tiles, 256), 256, 0, run_next_head_kernel, first.p, tiles, n,
+                  next.p);
+        const size_t smem = sizeof(uint64_t) * kRunTilePad * NW + sizeof(uint32_t) * (kRunTile / 32 + 8) + 16;
+        MH_CUDA(cudaFuncSetAttribute(runs_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MH_LAUNCH_B(ctx, "runs", n * 8 * NW, (unsigned)tiles, kRunThreads, smem, runs_kernel<NW>, sorted, n, K1, d,
+                    spectrum, n_spectrum, next.p, big_k.p, big_c.p, cap, status.p, counter.p,
+                    (unsigned long long*)totals.p, ctx->d_status);
+        // the last tile's inclusive count is the number of outputs
+        uint64_t last;
+        read_u64(ctx, status.p + (tiles - 1), &last, 1);
+        S = last & kRunCountMask;
+        read_u64(ctx, totals.p, tot, 2);
+    }
     *n_out = S;
-    *n_canon_runs = tot[1];
-    *n_palin_runs = tot[2];
+    *n_canon_runs = tot[0];
+    *n_palin_runs = tot[1];
+    first.reset();
+    next.reset();
+    status.reset();
     Buf<uint64_t> keys(ctx, (S ? S : 1) * NW), alt(ctx, (S ? S : 1) * NW);
     Buf<uint32_t> cnt(ctx, S ? S : 1), calt(ctx, S ? S : 1);
-    if (n && S)
-        MH_LAUNCH(ctx, "runs_write", (unsigned)tiles, kRunThreads, 0, runs_write_kernel<NW>, sorted, n, K1, d, spectrum,
-                  n_spectrum, tile_off.p, keys.p, cnt.p, ctx->d_status);
+    if (S)
+        MH_LAUNCH(ctx, "runs_compact", grid_for(ctx, S, 256), 256, 0, copy_keys_counts_kernel<NW>, big_k.p, big_c.p, S,
+                  keys.p, cnt.p);
+    big_k.reset();
+    big_c.reset();
     bool in_alt = radix_sort<NW>(ctx, keys.p, alt.p, cnt.p, calt.p, S, 0, 2 * K1);
     if (in_alt) {
         out_keys = std::move(alt);

@@ -376,6 +376,55 @@ __device__ __forceinline__ void st_relaxed_u32(uint32_t* p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// ------------------------------------------------------------ searching
+// First index in [0, n) with a[i] >= q, searched outward from `hint` (any
+// value in [0, n]): exponential steps towards the answer, then bisection.
+template <int NW>
+__device__ __forceinline__ uint64_t gallop_lb(const uint64_t* __restrict__ a, uint64_t n, const Key<NW>& q,
+                                              uint64_t hint) {
+    uint64_t lo, hi;  // answer in [lo, hi]
+    if (hint < n && key_less<NW>(load_key<NW>(a, hint), q)) {
+        // a[hint] < q: answer > hint
+        lo = hint + 1;
+        uint64_t step = 1;
+        while (true) {
+            uint64_t probe = lo + step - 1;
+            if (probe >= n) {
+                hi = n;
+                break;
+            }
+            if (!key_less<NW>(load_key<NW>(a, probe), q)) {
+                hi = probe;
+                break;
+            }
+            lo = probe + 1;
+            step <<= 1;
+        }
+    } else {
+        // a[hint] >= q (or hint == n): answer <= hint
+        hi = hint;
+        uint64_t step = 1;
+        while (true) {
+            if (hi < step) {
+                lo = 0;
+                break;
+            }
+            uint64_t probe = hi - step;
+            if (key_less<NW>(load_key<NW>(a, probe), q)) {
+                lo = probe + 1;
+                break;
+            }
+            hi = probe;
+            step <<= 1;
+        }
+    }
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (key_less<NW>(load_key<NW>(a, mid), q)) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
 // ----------------------------------------------------------- hashing
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;

@@ -161,6 +161,19 @@ def test_tile_boundaries(mh, ctx, n_windows):
     _compare_all(mh, ctx, ascii, offs, k, 1)
 
 
+@pytest.mark.parametrize("n_reads", [300, 1500, 3000])
+def test_shared_prefix_groups(mh, ctx, n_reads):
+    """Distinct keys sharing their top 40 bits (a 20-base common prefix): the
+    sorts run their LSD passes over the top bits only and must put such groups
+    in order afterwards (in shared memory, or by segment passes when a group is
+    larger than a tile)."""
+    rng = np.random.default_rng(n_reads)
+    reads = ["A" * 20 + "".join(rng.choice(list("CGT"), size=12)) for _ in range(n_reads)]
+    ascii, offs = synth.reads_from_strings(reads + reads)
+    _compare_all(mh, ctx, ascii, offs, 31, 2)
+    _compare_all(mh, ctx, ascii, offs, 25, 1)
+
+
 def test_empty_and_short_inputs(mh, ctx):
     for reads in ([], [""], ["ACG"], ["NNNN", "AC"], ["ACGTACGTAC"]):
         ascii, offs = synth.reads_from_strings(reads)
