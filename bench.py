@@ -319,8 +319,9 @@ def main():
     rec = _traffic_record()
     traffic = None
     if rec and launches:
-        keys_per_launch = o_bytes / launches / 16.0
-        traffic = rec["dram_bytes_per_key"] * keys_per_launch
+        # DRAM bytes per algorithmic byte of the captured launch, times the
+        # algorithmic bytes of an average timed launch
+        traffic = rec["dram_bytes_per_key"] / rec["algorithmic_bytes_per_key"] * (o_bytes / launches)
     roofline = {"bound": "hbm", "kernel": "radix_onesweep", "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "algorithmic_bytes_per_launch": (o_bytes / launches) if launches else 0,

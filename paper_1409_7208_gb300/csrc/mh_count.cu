@@ -237,33 +237,41 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
         total += wsum[w];
     }
     const uint32_t excl_thread = wpre + x - outs;
-    if (tid == 0) {
+    if (warp == 0) {
+        // warp-wide look-back: lane l reads the status of tile (j - l); the
+        // window is used up to the nearest tile with an inclusive count
         uint64_t* st = status + tile;
-        st_relaxed_u64(st, (tile == 0 ? kRunInc : kRunAgg) | total);
+        if (lane == 0) st_relaxed_u64(st, (tile == 0 ? kRunInc : kRunAgg) | total);
         uint64_t excl = 0;
-        if (tile > 0) {
-            int64_t j = (int64_t)tile - 1;
-            bool ok = true;
-            while (j >= 0) {
-                uint64_t v = ld_relaxed_u64(status + j);
-                int spins = 0;
-                while ((v & ~kRunCountMask) == 0) {
-                    if (++spins > (1 << 23)) {
-                        ok = false;
-                        break;
-                    }
-                    if (spins > 64) __nanosleep(128);
-                    v = ld_relaxed_u64(status + j);
+        bool ok = true;
+        for (int64_t j = (int64_t)tile - 1; j >= 0 && ok; j -= 32) {
+            const int64_t idx = j - lane;
+            uint64_t v = idx >= 0 ? ld_relaxed_u64(status + idx) : kRunInc;
+            int spins = 0;
+            uint32_t inc;
+            while (true) {
+                inc = __ballot_sync(0xFFFFFFFFu, (v & ~kRunCountMask) == kRunInc);
+                const uint32_t need = inc ? ((inc & (0u - inc)) << 1) - 1u : 0xFFFFFFFFu;  // lanes 0..nearest INC
+                const uint32_t waiting = __ballot_sync(0xFFFFFFFFu, (v & ~kRunCountMask) == 0) & need;
+                if (!waiting) break;
+                if (++spins > (1 << 23)) {
+                    ok = false;
+                    break;
                 }
-                if (!ok) break;
-                excl += v & kRunCountMask;
-                if ((v & ~kRunCountMask) == kRunInc) break;
-                j--;
+                if (spins > 64) __nanosleep(128);
+                if (idx >= 0 && (v & ~kRunCountMask) == 0) v = ld_relaxed_u64(status + idx);
             }
-            if (!ok) atomicOr(err, ST_SPIN_TIMEOUT);
-            st_relaxed_u64(st, kRunInc | (excl + total));
+            const uint32_t need = inc ? ((inc & (0u - inc)) << 1) - 1u : 0xFFFFFFFFu;
+            uint64_t c = ((need >> lane) & 1u) ? (v & kRunCountMask) : 0;
+            for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, off);
+            excl += c;
+            if (inc) break;
         }
-        *tile_off = excl;
+        if (lane == 0) {
+            if (!ok) atomicOr(err, ST_SPIN_TIMEOUT);
+            if (tile > 0) st_relaxed_u64(st, kRunInc | (excl + total));
+            *tile_off = excl;
+        }
     }
     // per-tile totals of runs and palindromic runs
     uint32_t hs = heads, ps = palins;

@@ -10,9 +10,11 @@
 //   ends     the edges with out0 or in0 (the graph's dead ends, a small
 //            fraction of S) go into a small open-addressing hash table with
 //            their two flags, which stays in L2.
-//   probe    warp per fragment, one window per lane: a probe of the small
-//            table per window; every window p without outdegree is recorded
-//            as a hit (its position and the end of its fragment).
+//   probe    warp per fragment, one window per lane: a bit test in a
+//            prefilter of the edges without outdegree (about 8 bits per dead
+//            end), and for the few positives a probe of the small table;
+//            every window p without outdegree is recorded as a hit (its
+//            position and the end of its fragment).
 //   walk     thread per hit: step forward to the next solid window q (probes
 //            of a hash set of the canonical solid keys); if q > p+1 and q
 //            has no indegree, the windows p+1..q-1 are emitted (canonical
@@ -75,17 +77,27 @@ __global__ void __launch_bounds__(256) degree_kernel(const uint64_t* __restrict_
     if ((threadIdx.x & 31) == 0 && ends) atomicAdd(n_ends, (unsigned long long)ends);
 }
 
-// Dead-end edges (oriented) with their flags into the small table.
+// Bit of the out0 prefilter for a key hash (bits 20.. of the hash; the
+// table slot uses the low bits, the tag the high 32).
+__device__ __forceinline__ uint64_t filter_bit(uint64_t h, uint64_t bits_mask) { return (h >> 20) & bits_mask; }
+
+// Dead-end edges (oriented) with their flags into the small table; edges
+// without outdegree also into the prefilter bitmap.
 template <int NW>
 __global__ void __launch_bounds__(256) ends_insert_kernel(const uint64_t* __restrict__ S, uint64_t n,
                                                           const uint8_t* __restrict__ flags,
                                                           Slot<NW>* __restrict__ table, uint64_t cap_mask,
+                                                          uint32_t* __restrict__ filter, uint64_t filter_mask,
                                                           uint32_t* __restrict__ err) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         uint8_t f = flags[i];
         if (!f) continue;
         Key<NW> x = load_key<NW>(S, i);
         uint64_t h = key_hash<NW>(x);
+        if (f & 1u) {
+            const uint64_t b = filter_bit(h, filter_mask);
+            atomicOr(&filter[b >> 5], 1u << (b & 31));
+        }
         uint32_t tag = slot_tag(h);
         uint64_t s = h & cap_mask;
         bool placed = false;
@@ -173,6 +185,7 @@ template <int NW>
 __global__ void __launch_bounds__(256) mercy_probe_kernel(const uint32_t* __restrict__ packed,
                                                           const uint64_t* __restrict__ frag_offs, uint64_t n_frags,
                                                           int k, const Slot<NW>* __restrict__ ends, uint64_t cap_mask,
+                                                          const uint32_t* __restrict__ filter, uint64_t filter_mask,
                                                           ulonglong2* __restrict__ hits, uint64_t hit_cap,
                                                           unsigned long long* __restrict__ n_hits) {
     const int lane = threadIdx.x & 31;
@@ -186,7 +199,11 @@ __global__ void __launch_bounds__(256) mercy_probe_kernel(const uint32_t* __rest
         for (uint64_t base = 0; base < nwin; base += 32) {
             const uint64_t p = base + lane;
             bool hit = false;
-            if (p < nwin) hit = (ends_find<NW>(ends, cap_mask, load_window<NW>(packed, b + p, K1)) & 1u) != 0;
+            if (p < nwin) {
+                const Key<NW> x = load_window<NW>(packed, b + p, K1);
+                const uint64_t fb = filter_bit(key_hash<NW>(x), filter_mask);
+                if ((__ldg(&filter[fb >> 5]) >> (fb & 31)) & 1u) hit = (ends_find<NW>(ends, cap_mask, x) & 1u) != 0;
+            }
             const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
             if (!m) continue;
             uint64_t first = 0;
@@ -256,9 +273,13 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
     const uint64_t cap = next_pow2(std::max<uint64_t>(2 * n_ends, 64));
     Buf<Slot<NW>> table(ctx, cap);
     table.zero();
+    // prefilter: about 8 bits per dead end (at least 2^20 bits)
+    const uint64_t fbits = next_pow2(std::max<uint64_t>(8 * n_ends, 1u << 20));
+    Buf<uint32_t> filter(ctx, fbits / 32);
+    filter.zero();
     if (n_ends)
         MH_LAUNCH(ctx, "mercy_ends_insert", grid_for(ctx, S, 256), 256, 0, ends_insert_kernel<NW>, solid->keys, S,
-                  flags.p, table.p, cap - 1, ctx->d_status);
+                  flags.p, table.p, cap - 1, filter.p, fbits - 1, ctx->d_status);
     flags.reset();
     // solidity set of the canonical solid keys, load <= 1/2 (<= 0.61 if all palindromes)
     const uint64_t scap = next_pow2(std::max<uint64_t>(S + S / 2, 64));
@@ -277,7 +298,7 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
         if (reads->n_frags && n_ends)
             MH_LAUNCH_B(ctx, "mercy_probe", reads->n_packed / 4, grid_for(ctx, reads->n_frags * 32, 256, 8), 256, 0,
                         mercy_probe_kernel<NW>, reads->packed, reads->frag_offs, reads->n_frags, k, table.p, cap - 1,
-                        hits.p, hit_cap, (unsigned long long*)(stats.p + 1));
+                        filter.p, fbits - 1, hits.p, hit_cap, (unsigned long long*)(stats.p + 1));
         read_u64(ctx, stats.p + 1, &n_hits, 1);
         if (n_hits <= hit_cap) break;
         hit_cap = n_hits;
