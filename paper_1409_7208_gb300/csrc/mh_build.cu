@@ -12,8 +12,9 @@
 //             entries; already ascending within each label, so one stable
 //             radix pass on their top 8 bits sorts them
 //   joins     zero indegree = B \ A, zero outdegree = A \ B (sorted queries
-//             in sorted arrays: each thread gallops through 16 consecutive
-//             queries)
+//             in sorted arrays: each thread gallops through 8 consecutive
+//             queries); B, A and the joins are tile compactions with a
+//             decoupled look-back
 //   padding   dummy entries (node $ v[0..k-2], label v[k-1]) sorted by
 //             (v[k-2..0], v[k-1]); $ entries in the order of A \ B
 //   merge     final position of every entry: its rank in its own list plus
@@ -84,11 +85,9 @@ __global__ void colex_kernel(const uint64_t* __restrict__ s, const uint32_t* __r
     }
 }
 
-// Per sorted entry: flags (bit0 minus, bit1 node head, bit2 node last in E),
-// and selection flags for B (heads) and A (unflagged entries).
+// Per sorted entry: flags (bit0 minus, bit1 node head, bit2 node last in E).
 template <int NW>
-__global__ void analyse_kernel(const uint64_t* __restrict__ ck, uint64_t E, uint8_t* __restrict__ fl,
-                               uint32_t* __restrict__ is_head, uint32_t* __restrict__ is_plain) {
+__global__ void analyse_kernel(const uint64_t* __restrict__ ck, uint64_t E, uint8_t* __restrict__ fl) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < E; i += (uint64_t)gridDim.x * blockDim.x) {
         Key<NW> x = load_key<NW>(ck, i);
         Key<NW> g = key_shr<NW>(x, 4), node = key_shr<NW>(x, 2);
@@ -105,57 +104,109 @@ __global__ void analyse_kernel(const uint64_t* __restrict__ ck, uint64_t E, uint
         bool head = i == 0 || !key_eq<NW>(key_shr<NW>(load_key<NW>(ck, i - 1), 2), node);
         bool last = i + 1 == E || !key_eq<NW>(key_shr<NW>(load_key<NW>(ck, i + 1), 2), node);
         fl[i] = (minus ? 1 : 0) | (head ? 2 : 0) | (last ? 4 : 0);
-        is_head[i] = head;
-        is_plain[i] = !minus;
     }
 }
 
+// Tile compaction: 256 threads x 8 consecutive entries per tile, a block
+// scan of the per-thread counts and a decoupled look-back for the tile's
+// output offset (one read of the input, no flag or position arrays).
+constexpr int kCmpItems = 8;
+constexpr int kCmpTile = 256 * kCmpItems;
+
+// Heads (new nodes) -> B = reversed source nodes; unflagged entries -> A =
+// reversed targets (label, e[k-1], ..., e[1]).  Two output streams.
 template <int NW>
-__global__ void select_nodes_targets_kernel(const uint64_t* __restrict__ ck, uint64_t E, int k,
-                                            const uint32_t* __restrict__ is_head, const uint64_t* __restrict__ pos_b,
-                                            const uint32_t* __restrict__ is_plain, const uint64_t* __restrict__ pos_a,
-                                            uint64_t* __restrict__ B, uint64_t* __restrict__ A) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < E; i += (uint64_t)gridDim.x * blockDim.x) {
-        Key<NW> x = load_key<NW>(ck, i);
-        if (is_head[i]) store_key<NW>(B, pos_b[i], key_shr<NW>(x, 2));
-        if (is_plain[i]) {
-            // reversed target (label, e[k-1], ..., e[1]) = label * 4^(k-1) + G
+__global__ void __launch_bounds__(256) nodes_targets_kernel(const uint64_t* __restrict__ ck,
+                                                            const uint8_t* __restrict__ fl, uint64_t E, int k,
+                                                            uint64_t* __restrict__ B, uint64_t* __restrict__ A,
+                                                            uint64_t* __restrict__ status_b,
+                                                            uint64_t* __restrict__ status_a,
+                                                            uint32_t* __restrict__ tile_counter,
+                                                            uint32_t* __restrict__ err) {
+    __shared__ uint32_t scratch[8];
+    __shared__ uint64_t offs[2];
+    __shared__ uint32_t s_tile;
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    const uint64_t i0 = tile * kCmpTile + (uint64_t)threadIdx.x * kCmpItems;
+    uint32_t hm = 0, pm = 0;
+#pragma unroll
+    for (int j = 0; j < kCmpItems; j++) {
+        if (i0 + j < E) {
+            const uint8_t f = fl[i0 + j];
+            hm |= ((f >> 1) & 1u) << j;
+            pm |= ((f & 1u) ^ 1u) << j;
+        }
+    }
+    uint32_t tot_b, tot_a;
+    const uint32_t eb = block_excl_scan_256(__popc(hm), scratch, &tot_b);
+    const uint32_t ea = block_excl_scan_256(__popc(pm), scratch, &tot_a);
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        const uint64_t o = warp_lookback_u64(status_b, tile, tot_b, err);
+        if ((threadIdx.x & 31) == 0) offs[0] = o;
+    } else if (warp == 1) {
+        const uint64_t o = warp_lookback_u64(status_a, tile, tot_a, err);
+        if ((threadIdx.x & 31) == 0) offs[1] = o;
+    }
+    __syncthreads();
+    uint64_t pb = offs[0] + eb, pa = offs[1] + ea;
+#pragma unroll
+    for (int j = 0; j < kCmpItems; j++) {
+        if (!(((hm | pm) >> j) & 1u)) continue;
+        const Key<NW> x = load_key<NW>(ck, i0 + j);
+        if ((hm >> j) & 1u) store_key<NW>(B, pb++, key_shr<NW>(x, 2));
+        if ((pm >> j) & 1u) {
             Key<NW> t = key_shr<NW>(x, 4);
             Key<NW> lab = key_zero<NW>();
             lab.w[0] = x.w[0] & 3u;
             lab = key_shl<NW>(lab, 2 * (k - 1));
 #pragma unroll
             for (int w = 0; w < NW; w++) t.w[w] |= lab.w[w];
-            store_key<NW>(A, pos_a[i], t);
+            store_key<NW>(A, pa++, t);
         }
     }
 }
 
-// flag[i] = 1 iff q[i] is absent from the sorted array a.  The queries are
-// sorted too: each thread takes 16 consecutive ones and gallops from the
-// previous answer.
-constexpr int kAbsentRun = 16;
+// The queries q (sorted) that are absent from the sorted array a, compacted
+// in order.  Each thread gallops through its 8 consecutive queries.
 template <int NW>
-__global__ void absent_kernel(const uint64_t* __restrict__ q, uint64_t nq, const uint64_t* __restrict__ a, uint64_t na,
-                              uint32_t* __restrict__ flag) {
-    for (uint64_t i0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) * kAbsentRun; i0 < nq;
-         i0 += (uint64_t)gridDim.x * blockDim.x * kAbsentRun) {
-        uint64_t hint = na / 2;
-        const uint64_t i1 = i0 + kAbsentRun < nq ? i0 + kAbsentRun : nq;
-        for (uint64_t i = i0; i < i1; i++) {
-            Key<NW> x = load_key<NW>(q, i);
-            uint64_t lb = gallop_lb<NW>(a, na, x, hint);
+__global__ void __launch_bounds__(256) absent_compact_kernel(const uint64_t* __restrict__ q, uint64_t nq,
+                                                             const uint64_t* __restrict__ a, uint64_t na,
+                                                             uint64_t* __restrict__ out,
+                                                             uint64_t* __restrict__ status,
+                                                             uint32_t* __restrict__ tile_counter,
+                                                             uint32_t* __restrict__ err) {
+    __shared__ uint32_t scratch[8];
+    __shared__ uint64_t off;
+    __shared__ uint32_t s_tile;
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    const uint64_t i0 = tile * kCmpTile + (uint64_t)threadIdx.x * kCmpItems;
+    uint32_t am = 0;
+    uint64_t hint = na / 2;
+#pragma unroll
+    for (int j = 0; j < kCmpItems; j++) {
+        if (i0 + j < nq) {
+            const Key<NW> x = load_key<NW>(q, i0 + j);
+            const uint64_t lb = gallop_lb<NW>(a, na, x, hint);
             hint = lb;
-            flag[i] = !(lb < na && key_eq<NW>(load_key<NW>(a, lb), x));
+            if (!(lb < na && key_eq<NW>(load_key<NW>(a, lb), x))) am |= 1u << j;
         }
     }
-}
-
-template <int NW>
-__global__ void select_kernel(const uint64_t* __restrict__ in, const uint32_t* __restrict__ flag,
-                              const uint64_t* __restrict__ pos, uint64_t n, uint64_t* __restrict__ out) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-        if (flag[i]) store_key<NW>(out, pos[i], load_key<NW>(in, i));
+    uint32_t tot;
+    const uint32_t e = block_excl_scan_256(__popc(am), scratch, &tot);
+    if ((threadIdx.x >> 5) == 0) {
+        const uint64_t o = warp_lookback_u64(status, tile, tot, err);
+        if ((threadIdx.x & 31) == 0) off = o;
+    }
+    __syncthreads();
+    uint64_t p = off + e;
+#pragma unroll
+    for (int j = 0; j < kCmpItems; j++)
+        if ((am >> j) & 1u) store_key<NW>(out, p++, load_key<NW>(q, i0 + j));
 }
 
 // zero-indegree reversed node v_rev -> dummy key (v[k-2], ..., v[0], v[k-1])
@@ -274,15 +325,6 @@ __global__ void pack_bits_kernel(const uint8_t* __restrict__ wf, uint64_t m, uin
     if (lane == 0 && cnt) atomicAdd(n_last, (unsigned long long)cnt);
 }
 
-// Exclusive positions of set flags: pos has n+1 entries, pos[n] = count.
-static uint64_t flag_positions(mh_ctx* ctx, const uint32_t* flag, uint64_t n, Buf<uint64_t>& pos) {
-    pos = Buf<uint64_t>(ctx, n + 1);
-    exclusive_scan_u32(ctx, flag, pos.p, n);
-    uint64_t c;
-    read_u64(ctx, pos.p + n, &c, 1);
-    return c;
-}
-
 template <int NW>
 void build_sdbg(mh_ctx* ctx, const mh_kmers* solid, const mh_kmers* mercy, mh_sdbg* out) {
     const int k = solid->k, K1 = k + 1;
@@ -309,44 +351,49 @@ void build_sdbg(mh_ctx* ctx, const mh_kmers* solid, const mh_kmers* mercy, mh_sd
     cv2.reset();
     // per-entry flags, node list B, target list A
     Buf<uint8_t> fl(ctx, E ? E : 1);
-    Buf<uint32_t> is_head(ctx, E ? E : 1), is_plain(ctx, E ? E : 1);
-    if (E)
-        MH_LAUNCH(ctx, "analyse", grid_for(ctx, E, 256), 256, 0, analyse_kernel<NW>, ck.p, E, fl.p, is_head.p,
-                  is_plain.p);
-    Buf<uint64_t> pos_b, pos_a;
-    const uint64_t nB = flag_positions(ctx, is_head.p, E, pos_b);
-    const uint64_t nA = flag_positions(ctx, is_plain.p, E, pos_a);
-    Buf<uint64_t> B(ctx, (nB ? nB : 1) * NW), A(ctx, (nA ? nA : 1) * NW), A2(ctx, (nA ? nA : 1) * NW);
-    if (E)
-        MH_LAUNCH(ctx, "select_nodes_targets", grid_for(ctx, E, 256), 256, 0, select_nodes_targets_kernel<NW>, ck.p, E,
-                  k, is_head.p, pos_b.p, is_plain.p, pos_a.p, B.p, A.p);
-    is_head.reset();
-    is_plain.reset();
-    pos_a.reset();
-    pos_b.reset();
+    if (E) MH_LAUNCH(ctx, "analyse", grid_for(ctx, E, 256), 256, 0, analyse_kernel<NW>, ck.p, E, fl.p);
+    Buf<uint64_t> B(ctx, (E ? E : 1) * NW), A(ctx, (E ? E : 1) * NW);
+    uint64_t nB = 0, nA = 0;
+    if (E) {
+        const uint64_t tiles = ceil_div(E, kCmpTile);
+        Buf<uint64_t> st(ctx, 2 * tiles);
+        Buf<uint32_t> counter(ctx, 1);
+        st.zero();
+        counter.zero();
+        MH_LAUNCH(ctx, "nodes_targets", (unsigned)tiles, 256, 0, nodes_targets_kernel<NW>, ck.p, fl.p, E, k, B.p, A.p,
+                  st.p, st.p + tiles, counter.p, ctx->d_status);
+        uint64_t last[2];
+        read_u64(ctx, st.p + tiles - 1, &last[0], 1);
+        read_u64(ctx, st.p + 2 * tiles - 1, &last[1], 1);
+        nB = last[0] & kLbCountMask;
+        nA = last[1] & kLbCountMask;
+    }
+    Buf<uint64_t> A2(ctx, (nA ? nA : 1) * NW);
     if (radix_sort<NW>(ctx, A.p, A2.p, nullptr, nullptr, nA, std::max(0, 2 * k - 8), 2 * k)) std::swap(A, A2);
     A2.reset();
     // zero indegree: B \ A; zero outdegree: A \ B
-    Buf<uint32_t> zf_b(ctx, nB ? nB : 1), zf_a(ctx, nA ? nA : 1);
-    if (nB)
-        MH_LAUNCH(ctx, "absent_nodes", grid_for(ctx, ceil_div(nB, kAbsentRun), 256), 256, 0, absent_kernel<NW>, B.p, nB,
-                  A.p, nA, zf_b.p);
-    if (nA)
-        MH_LAUNCH(ctx, "absent_targets", grid_for(ctx, ceil_div(nA, kAbsentRun), 256), 256, 0, absent_kernel<NW>, A.p,
-                  nA, B.p, nB, zf_a.p);
-    Buf<uint64_t> pz_b, pz_a;
-    const uint64_t t = flag_positions(ctx, zf_b.p, nB, pz_b);
-    const uint64_t u = flag_positions(ctx, zf_a.p, nA, pz_a);
-    Buf<uint64_t> zin(ctx, (t ? t : 1) * NW), zout(ctx, (u ? u : 1) * NW);
-    if (nB) MH_LAUNCH(ctx, "select_zin", grid_for(ctx, nB, 256), 256, 0, select_kernel<NW>, B.p, zf_b.p, pz_b.p, nB, zin.p);
-    if (nA)
-        MH_LAUNCH(ctx, "select_zout", grid_for(ctx, nA, 256), 256, 0, select_kernel<NW>, A.p, zf_a.p, pz_a.p, nA, zout.p);
+    Buf<uint64_t> zin(ctx, (nB ? nB : 1) * NW), zout(ctx, (nA ? nA : 1) * NW);
+    uint64_t t = 0, u = 0;
+    {
+        const uint64_t tb = ceil_div(nB ? nB : 1, kCmpTile), ta = ceil_div(nA ? nA : 1, kCmpTile);
+        Buf<uint64_t> st(ctx, tb + ta);
+        Buf<uint32_t> counter(ctx, 2);
+        st.zero();
+        counter.zero();
+        if (nB)
+            MH_LAUNCH(ctx, "absent_nodes", (unsigned)tb, 256, 0, absent_compact_kernel<NW>, B.p, nB, A.p, nA, zin.p,
+                      st.p, counter.p, ctx->d_status);
+        if (nA)
+            MH_LAUNCH(ctx, "absent_targets", (unsigned)ta, 256, 0, absent_compact_kernel<NW>, A.p, nA, B.p, nB, zout.p,
+                      st.p + tb, counter.p + 1, ctx->d_status);
+        uint64_t last[2] = {0, 0};
+        if (nB) read_u64(ctx, st.p + tb - 1, &last[0], 1);
+        if (nA) read_u64(ctx, st.p + tb + ta - 1, &last[1], 1);
+        t = last[0] & kLbCountMask;
+        u = last[1] & kLbCountMask;
+    }
     B.reset();
     A.reset();
-    zf_a.reset();
-    zf_b.reset();
-    pz_a.reset();
-    pz_b.reset();
     // dummy entries in colex order
     Buf<uint64_t> dk(ctx, (t ? t : 1) * NW), dk2(ctx, (t ? t : 1) * NW);
     if (t) MH_LAUNCH(ctx, "dummy_keys", grid_for(ctx, t, 256), 256, 0, dummy_keys_kernel<NW>, zin.p, t, k, dk.p);

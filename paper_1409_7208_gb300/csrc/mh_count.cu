@@ -8,7 +8,9 @@
 // when x = rc(x) (a palindrome, counted twice per occurrence).
 //
 //   extract   warp per fragment, window keys from the packed words, canonical
-//   sort      LSD radix over the 2(k+1) key bits
+//             (1-word keys: through the invertible mixer mix_bij)
+//   sort      LSD radix over the 2(k+1) key bits; for mixed 1-word keys over
+//             the top ceil(log2 n) + 8 bits plus a fix-up of shared prefixes
 //   runs      run heads in a shared-memory bitmask, run lengths from the
 //             next head, solid filter, outputs placed by decoupled look-back
 //   expand    each solid canonical key -> itself and its reverse complement
@@ -27,8 +29,9 @@ __global__ void frag_windows_kernel(const uint64_t* __restrict__ frag_offs, uint
     }
 }
 
-// Warp per fragment: canonical key of every window, written at woff[f] + i.
-template <int NW>
+// Warp per fragment: canonical key of every window, written at woff[f] + i
+// (MIXED: its mix_bij image, 1-word keys).
+template <int NW, bool MIXED>
 __global__ void __launch_bounds__(256) extract_canonical_kernel(const uint32_t* __restrict__ packed,
                                                                 const uint64_t* __restrict__ frag_offs,
                                                                 const uint64_t* __restrict__ woff, uint64_t n_frags,
@@ -43,7 +46,9 @@ __global__ void __launch_bounds__(256) extract_canonical_kernel(const uint32_t* 
         for (uint64_t i = lane; i < nw; i += 32) {
             Key<NW> x = load_window<NW>(packed, b + i, K1);
             Key<NW> r = key_rc<NW>(x, K1);
-            store_key<NW>(out, w0 + i, key_less<NW>(r, x) ? r : x);
+            Key<NW> c = key_less<NW>(r, x) ? r : x;
+            if constexpr (MIXED) c.w[0] = mix_bij(c.w[0]);
+            store_key<NW>(out, w0 + i, c);
         }
     }
 }
@@ -56,23 +61,11 @@ __global__ void __launch_bounds__(256) extract_canonical_kernel(const uint32_t* 
 // outputs are placed with a decoupled look-back over per-tile output counts.
 
 constexpr int kRunThreads = 256;
-constexpr int kRunItems = 16;
+constexpr int kRunItems = 8;
 constexpr int kRunTile = kRunThreads * kRunItems;  // keys per tile
 constexpr int kRunTilePad = kRunTile + kRunTile / 16;
 __device__ __forceinline__ uint32_t rp(uint32_t i) { return i + (i >> 4); }
 constexpr uint64_t kNoHead = ~0ull;
-constexpr uint64_t kRunAgg = 1ull << 62;
-constexpr uint64_t kRunInc = 2ull << 62;
-constexpr uint64_t kRunCountMask = (1ull << 62) - 1;
-
-__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
-    uint64_t v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
 
 // first[t] = index of the first run head in tile t, or kNoHead (warp per tile).
 template <int NW>
@@ -108,21 +101,39 @@ __global__ void run_next_head_kernel(const uint64_t* __restrict__ first, uint64_
     }
 }
 
+// Number of copies of x in the sorted spectrum (of mix_bij images when
+// spec_mixed), searching outward from `hint` and leaving it after the copies:
+// a thread's queries ascend, so each search starts near the previous answer.
 template <int NW>
-__device__ __forceinline__ uint64_t spectrum_count(const uint64_t* __restrict__ spec, uint64_t n_spec,
-                                                   const Key<NW>& x) {
-    uint64_t lo = 0, hi = n_spec;
-    while (lo < hi) {
-        uint64_t mid = (lo + hi) >> 1;
-        if (key_less<NW>(load_key<NW>(spec, mid), x)) lo = mid + 1; else hi = mid;
+__device__ __forceinline__ uint64_t spectrum_count(const uint64_t* __restrict__ spec, uint64_t n_spec, Key<NW> x,
+                                                   bool spec_mixed, uint64_t& hint) {
+    if (spec_mixed) x.w[0] = mix_bij(x.w[0]);
+    const uint64_t lb = gallop_lb<NW>(spec, n_spec, x, hint);
+    if (lb >= n_spec || !key_eq<NW>(load_key<NW>(spec, lb), x)) {
+        hint = lb;
+        return 0;
     }
-    const uint64_t first = lo;
-    hi = n_spec;
-    while (lo < hi) {
-        uint64_t mid = (lo + hi) >> 1;
-        if (key_less<NW>(x, load_key<NW>(spec, mid))) hi = mid; else lo = mid + 1;
+    // first index after lb holding another key
+    uint64_t lo = lb, step = 1, hi;
+    while (true) {
+        const uint64_t probe = lo + step;
+        if (probe >= n_spec) {
+            hi = n_spec;
+            break;
+        }
+        if (!key_eq<NW>(load_key<NW>(spec, probe), x)) {
+            hi = probe;
+            break;
+        }
+        lo = probe;
+        step <<= 1;
     }
-    return lo - first;
+    while (hi - lo > 1) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (key_eq<NW>(load_key<NW>(spec, mid), x)) lo = mid; else hi = mid;
+    }
+    hint = hi;
+    return hi - lb;
 }
 
 // Counting mode (spec == nullptr): a run of length len is the canonical key
@@ -130,9 +141,10 @@ __device__ __forceinline__ uint64_t spectrum_count(const uint64_t* __restrict__ 
 // kept if the count is >= d.  Lookup mode: every run is kept and its count
 // is looked up in the spectrum.  A kept run outputs the key and, unless it is
 // a palindrome, its reverse complement, both with the count.
-template <int NW>
+template <int NW, bool IN_MIXED>
 __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __restrict__ s, uint64_t n, int K1, int d,
                                                            const uint64_t* __restrict__ spec, uint64_t n_spec,
+                                                           bool spec_mixed,
                                                            const uint64_t* __restrict__ next_head,
                                                            uint64_t* __restrict__ out_keys,
                                                            uint32_t* __restrict__ out_cnt, uint64_t out_cap,
@@ -147,7 +159,9 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
     uint32_t* head_bits = reinterpret_cast<uint32_t*>(tk + kRunTilePad * NW);  // [TILE / 32]
     uint32_t* wsum = head_bits + kRunTile / 32;                              // [8]
     uint64_t* tile_off = reinterpret_cast<uint64_t*>(wsum + 8);             // [1]
-    uint32_t* tile_id = reinterpret_cast<uint32_t*>(tile_off + 1);          // [1]
+    uint32_t* tile_id = reinterpret_cast<uint32_t*>(tile_off + 1);          // [1] (+1 pad)
+    uint64_t* out_stage_k = reinterpret_cast<uint64_t*>(tile_id + 2);       // [TILE] if NW == 1
+    uint32_t* out_stage_c = reinterpret_cast<uint32_t*>(out_stage_k + (NW == 1 ? kRunTile : 0));  // [TILE]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) *tile_id = atomicAdd(tile_counter, 1u);
     __syncthreads();
@@ -183,9 +197,10 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
     // each thread: kRunItems consecutive keys
     const uint32_t i0 = tid * kRunItems;
     uint32_t outs = 0, heads = 0, palins = 0;
-    uint32_t hmask = i0 < tn ? (head_bits[i0 >> 5] >> (i0 & 31)) & 0xFFFFu : 0u;  // kRunItems == 16
+    uint32_t hmask = i0 < tn ? (head_bits[i0 >> 5] >> (i0 & 31)) & ((1u << kRunItems) - 1u) : 0u;
     uint32_t cnt[kRunItems];
     uint8_t nout[kRunItems];
+    uint64_t hint = n_spec / 2;
 #pragma unroll
     for (int j = 0; j < kRunItems; j++) {
         nout[j] = 0;
@@ -208,8 +223,9 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
         Key<NW> x;
 #pragma unroll
         for (int w = 0; w < NW; w++) x.w[w] = tk[rp(i) * NW + w];
+        if constexpr (IN_MIXED) x.w[0] = unmix_bij(x.w[0]);
         const bool palin = key_eq<NW>(key_rc<NW>(x, K1), x);
-        const uint64_t len = spec ? spectrum_count<NW>(spec, n_spec, x) : end - (start + i);
+        const uint64_t len = spec ? spectrum_count<NW>(spec, n_spec, x, spec_mixed, hint) : end - (start + i);
         uint64_t c = palin ? 2 * len : len;
         if (c > 0xFFFFFFFFull) {
             atomicOr(err, ST_OVERFLOW);
@@ -238,40 +254,8 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
     }
     const uint32_t excl_thread = wpre + x - outs;
     if (warp == 0) {
-        // warp-wide look-back: lane l reads the status of tile (j - l); the
-        // window is used up to the nearest tile with an inclusive count
-        uint64_t* st = status + tile;
-        if (lane == 0) st_relaxed_u64(st, (tile == 0 ? kRunInc : kRunAgg) | total);
-        uint64_t excl = 0;
-        bool ok = true;
-        for (int64_t j = (int64_t)tile - 1; j >= 0 && ok; j -= 32) {
-            const int64_t idx = j - lane;
-            uint64_t v = idx >= 0 ? ld_relaxed_u64(status + idx) : kRunInc;
-            int spins = 0;
-            uint32_t inc;
-            while (true) {
-                inc = __ballot_sync(0xFFFFFFFFu, (v & ~kRunCountMask) == kRunInc);
-                const uint32_t need = inc ? ((inc & (0u - inc)) << 1) - 1u : 0xFFFFFFFFu;  // lanes 0..nearest INC
-                const uint32_t waiting = __ballot_sync(0xFFFFFFFFu, (v & ~kRunCountMask) == 0) & need;
-                if (!waiting) break;
-                if (++spins > (1 << 23)) {
-                    ok = false;
-                    break;
-                }
-                if (spins > 64) __nanosleep(128);
-                if (idx >= 0 && (v & ~kRunCountMask) == 0) v = ld_relaxed_u64(status + idx);
-            }
-            const uint32_t need = inc ? ((inc & (0u - inc)) << 1) - 1u : 0xFFFFFFFFu;
-            uint64_t c = ((need >> lane) & 1u) ? (v & kRunCountMask) : 0;
-            for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, off);
-            excl += c;
-            if (inc) break;
-        }
-        if (lane == 0) {
-            if (!ok) atomicOr(err, ST_SPIN_TIMEOUT);
-            if (tile > 0) st_relaxed_u64(st, kRunInc | (excl + total));
-            *tile_off = excl;
-        }
+        const uint64_t excl = warp_lookback_u64(status, tile, total, err);
+        if (lane == 0) *tile_off = excl;
     }
     // per-tile totals of runs and palindromic runs
     uint32_t hs = heads, ps = palins;
@@ -284,11 +268,16 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
         atomicAdd(&totals[1], (unsigned long long)ps);
     }
     __syncthreads();
-    uint64_t pos = *tile_off + excl_thread;
-    if (pos + outs > out_cap) {
-        if (outs) atomicOr(err, ST_TABLE_FULL);
+    const uint64_t toff = *tile_off;
+    if (toff + total > out_cap) {
+        if (tid == 0 && total) atomicOr(err, ST_TABLE_FULL);
         return;
     }
+    // a tile's outputs fill [toff, toff + total): for 1-word keys that fit,
+    // stage them in shared memory and write them out coalesced
+    const bool staged = NW == 1 && total <= (uint32_t)kRunTile;
+    uint32_t lpos = excl_thread;
+    uint64_t pos = toff + excl_thread;
 #pragma unroll
     for (int j = 0; j < kRunItems; j++) {
         if (!nout[j]) continue;
@@ -296,13 +285,25 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
         Key<NW> xk;
 #pragma unroll
         for (int w = 0; w < NW; w++) xk.w[w] = tk[rp(i) * NW + w];
-        store_key<NW>(out_keys, pos, xk);
-        out_cnt[pos] = cnt[j];
-        pos++;
-        if (nout[j] == 2) {
-            store_key<NW>(out_keys, pos, key_rc<NW>(xk, K1));
-            out_cnt[pos] = cnt[j];
-            pos++;
+        if constexpr (IN_MIXED) xk.w[0] = unmix_bij(xk.w[0]);
+        for (uint32_t o = 0; o < nout[j]; o++) {
+            const Key<NW> y = o == 0 ? xk : key_rc<NW>(xk, K1);
+            if (staged) {
+                out_stage_k[lpos] = y.w[0];
+                out_stage_c[lpos] = cnt[j];
+                lpos++;
+            } else {
+                store_key<NW>(out_keys, pos, y);
+                out_cnt[pos] = cnt[j];
+                pos++;
+            }
+        }
+    }
+    if (staged) {
+        __syncthreads();
+        for (uint32_t i = tid; i < total; i += kRunThreads) {
+            out_keys[toff + i] = out_stage_k[i];
+            out_cnt[toff + i] = out_stage_c[i];
         }
     }
 }
@@ -322,7 +323,8 @@ __global__ void copy_keys_counts_kernel(const uint64_t* __restrict__ k, const ui
 template <int NW>
 void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, Buf<uint64_t>& out_keys,
                  Buf<uint32_t>& out_cnt, uint64_t* n_out, uint64_t* n_canon_runs, uint64_t* n_palin_runs,
-                 const uint64_t* spectrum, uint64_t n_spectrum) {
+                 const uint64_t* spectrum, uint64_t n_spectrum, bool in_mixed, bool spec_mixed) {
+    if (NW != 1 && (in_mixed || spec_mixed)) fail(MH_EUNSUPPORTED, "mixed keys are 1-word keys");
     const int K1 = k + 1;
     const uint64_t tiles = ceil_div(n ? n : 1, kRunTile);
     // outputs: <= n when every kept run has >= 2 keys or is a palindrome (d >= 2), else <= 2n
@@ -340,15 +342,17 @@ void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, 
                   tiles, first.p);
         MH_LAUNCH(ctx, "runs_next_head", grid_for(ctx, tiles, 256), 256, 0, run_next_head_kernel, first.p, tiles, n,
                   next.p);
-        const size_t smem = sizeof(uint64_t) * kRunTilePad * NW + sizeof(uint32_t) * (kRunTile / 32 + 8) + 16;
-        MH_CUDA(cudaFuncSetAttribute(runs_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        MH_LAUNCH_B(ctx, "runs", n * 8 * NW, (unsigned)tiles, kRunThreads, smem, runs_kernel<NW>, sorted, n, K1, d,
-                    spectrum, n_spectrum, next.p, big_k.p, big_c.p, cap, status.p, counter.p,
+        const size_t smem = sizeof(uint64_t) * kRunTilePad * NW + sizeof(uint32_t) * (kRunTile / 32 + 8) + 16 +
+                            (NW == 1 ? (sizeof(uint64_t) + sizeof(uint32_t)) * kRunTile : 0);
+        auto kern = in_mixed ? runs_kernel<NW, true> : runs_kernel<NW, false>;
+        MH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MH_LAUNCH_B(ctx, "runs", n * 8 * NW, (unsigned)tiles, kRunThreads, smem, kern, sorted, n, K1, d, spectrum,
+                    n_spectrum, spec_mixed, next.p, big_k.p, big_c.p, cap, status.p, counter.p,
                     (unsigned long long*)totals.p, ctx->d_status);
         // the last tile's inclusive count is the number of outputs
         uint64_t last;
         read_u64(ctx, status.p + (tiles - 1), &last, 1);
-        S = last & kRunCountMask;
+        S = last & kLbCountMask;
         read_u64(ctx, totals.p, tot, 2);
     }
     *n_out = S;
@@ -375,11 +379,11 @@ void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, 
 }
 
 template void expand_runs<1>(mh_ctx*, const uint64_t*, uint64_t, int, int, Buf<uint64_t>&, Buf<uint32_t>&, uint64_t*,
-                             uint64_t*, uint64_t*, const uint64_t*, uint64_t);
+                             uint64_t*, uint64_t*, const uint64_t*, uint64_t, bool, bool);
 template void expand_runs<2>(mh_ctx*, const uint64_t*, uint64_t, int, int, Buf<uint64_t>&, Buf<uint32_t>&, uint64_t*,
-                             uint64_t*, uint64_t*, const uint64_t*, uint64_t);
+                             uint64_t*, uint64_t*, const uint64_t*, uint64_t, bool, bool);
 template void expand_runs<4>(mh_ctx*, const uint64_t*, uint64_t, int, int, Buf<uint64_t>&, Buf<uint32_t>&, uint64_t*,
-                             uint64_t*, uint64_t*, const uint64_t*, uint64_t);
+                             uint64_t*, uint64_t*, const uint64_t*, uint64_t, bool, bool);
 
 template <int NW>
 void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out) {
@@ -392,18 +396,22 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
     uint64_t n;
     read_u64(ctx, woff.p + F, &n, 1);
     nwin.reset();
+    // 1-word keys are sorted through mix_bij: spread top bits let the sort
+    // run its passes over the top ceil(log2 n) + 8 bits only
+    constexpr bool kMixed = NW == 1;
     Buf<uint64_t> keys(ctx, (n ? n : 1) * NW), alt(ctx, (n ? n : 1) * NW);
     if (n)
         MH_LAUNCH_B(ctx, "extract_canonical", reads->n_packed / 4 + n * 8 * NW, grid_for(ctx, F * 32, 256, 8), 256, 0,
-                    extract_canonical_kernel<NW>, reads->packed, reads->frag_offs, woff.p, F, k, keys.p);
+                    (extract_canonical_kernel<NW, kMixed>), reads->packed, reads->frag_offs, woff.p, F, k, keys.p);
     woff.reset();
-    bool in_alt = radix_sort<NW>(ctx, keys.p, alt.p, nullptr, nullptr, n, 0, 2 * (k + 1));
+    bool in_alt = kMixed ? radix_sort_spread(ctx, keys.p, alt.p, n)
+                         : radix_sort<NW>(ctx, keys.p, alt.p, nullptr, nullptr, n, 0, 2 * (k + 1));
     Buf<uint64_t>& spec = in_alt ? alt : keys;
     (in_alt ? keys : alt).reset();
     Buf<uint64_t> sk;
     Buf<uint32_t> sc;
     uint64_t S = 0, runs = 0, palins = 0;
-    expand_runs<NW>(ctx, spec.p, n, k, d, sk, sc, &S, &runs, &palins, nullptr, 0);
+    expand_runs<NW>(ctx, spec.p, n, k, d, sk, sc, &S, &runs, &palins, nullptr, 0, kMixed, false);
     sync_and_check(ctx);
     out->k = k;
     out->nw = NW;
@@ -414,6 +422,7 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
     out->keys = sk.release();
     out->counts = sc.release();
     out->n_spectrum = n;
+    out->spectrum_mixed = kMixed;
     out->spectrum = spec.release();
 }
 

@@ -90,6 +90,7 @@ struct mh_kmers {
     // window, with repeats) kept for the mercy counts
     uint64_t* spectrum = nullptr;
     uint64_t n_spectrum = 0;
+    bool spectrum_mixed = false;  // spectrum holds mix_bij(canonical), sorted
     uint64_t n_kmers = 0, n_distinct = 0;
     mh_ctx* ctx = nullptr;
 };
@@ -425,12 +426,110 @@ __device__ __forceinline__ uint64_t gallop_lb(const uint64_t* __restrict__ a, ui
     return lo;
 }
 
+// ------------------------------------------------ tile compaction helpers
+// 64-bit per-tile status words for decoupled look-back: flag in the top two
+// bits (aggregate / inclusive), count in the low 62.
+constexpr uint64_t kLbAgg = 1ull << 62;
+constexpr uint64_t kLbInc = 2ull << 62;
+constexpr uint64_t kLbCountMask = (1ull << 62) - 1;
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Called by one whole warp of the tile: publishes the tile's total, looks
+// back over earlier tiles (lane l reads tile j - l, the window is used up to
+// the nearest inclusive entry; every wait is bounded) and returns the sum of
+// all earlier tiles' totals.  Tiles must be numbered in launch-claim order
+// (a dynamic tile id) so that every earlier tile is running or done.
+__device__ __forceinline__ uint64_t warp_lookback_u64(uint64_t* status, uint64_t tile, uint64_t total,
+                                                      uint32_t* err) {
+    const int lane = threadIdx.x & 31;
+    uint64_t* st = status + tile;
+    if (lane == 0) st_relaxed_u64(st, (tile == 0 ? kLbInc : kLbAgg) | total);
+    uint64_t excl = 0;
+    bool ok = true;
+    for (int64_t j = (int64_t)tile - 1; j >= 0 && ok; j -= 32) {
+        const int64_t idx = j - lane;
+        uint64_t v = idx >= 0 ? ld_relaxed_u64(status + idx) : kLbInc;
+        int spins = 0;
+        uint32_t inc;
+        while (true) {
+            inc = __ballot_sync(0xFFFFFFFFu, (v & ~kLbCountMask) == kLbInc);
+            const uint32_t need = inc ? ((inc & (0u - inc)) << 1) - 1u : 0xFFFFFFFFu;
+            const uint32_t waiting = __ballot_sync(0xFFFFFFFFu, (v & ~kLbCountMask) == 0) & need;
+            if (!waiting) break;
+            if (++spins > (1 << 23)) {
+                ok = false;
+                break;
+            }
+            if (spins > 64) __nanosleep(128);
+            if (idx >= 0 && (v & ~kLbCountMask) == 0) v = ld_relaxed_u64(status + idx);
+        }
+        const uint32_t need = inc ? ((inc & (0u - inc)) << 1) - 1u : 0xFFFFFFFFu;
+        uint64_t c = ((need >> lane) & 1u) ? (v & kLbCountMask) : 0;
+        for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, off);
+        excl += c;
+        if (inc) break;
+    }
+    if (lane == 0) {
+        if (!ok) atomicOr(err, 1u);  // ST_SPIN_TIMEOUT
+        if (tile > 0) st_relaxed_u64(st, kLbInc | (excl + total));
+    }
+    return excl;
+}
+
+// Exclusive prefix of a per-thread count over a block of 256 threads (8
+// warps); `scratch` holds 8 words of shared memory.  Also returns the total.
+__device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t* scratch, uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) scratch[warp] = x;
+    __syncthreads();
+    uint32_t pre = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < 8; w++) {
+        const uint32_t sw = scratch[w];
+        pre += w < warp ? sw : 0u;
+        tot += sw;
+    }
+    __syncthreads();
+    *total = tot;
+    return pre + x - v;
+}
+
 // ----------------------------------------------------------- hashing
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
 }
+// Invertible 64-bit mixer: odd multipliers and a 32-bit xorshift are each
+// bijections of 64-bit words, so mix_bij permutes the keys (equal keys stay
+// equal, distinct keys stay distinct) while spreading their top bits.
+constexpr uint64_t kMixC1 = 0x9E3779B97F4A7C15ull, kMixC2 = 0xBF58476D1CE4E5B9ull;
+constexpr uint64_t kMixC1Inv = 0xF1DE83E19937733Dull, kMixC2Inv = 0x96DE1B173F119089ull;  // inverses mod 2^64
+__host__ __device__ __forceinline__ uint64_t mix_bij(uint64_t x) {
+    x *= kMixC1;
+    x ^= x >> 32;
+    return x * kMixC2;
+}
+__host__ __device__ __forceinline__ uint64_t unmix_bij(uint64_t h) {
+    h *= kMixC2Inv;
+    h ^= h >> 32;
+    return h * kMixC1Inv;
+}
+
 template <int NW>
 __device__ __forceinline__ uint64_t key_hash(const Key<NW>& a) {
     uint64_t h = 0x9E3779B97F4A7C15ull;
@@ -448,6 +547,12 @@ template <int NW>
 bool radix_sort(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt, uint64_t n,
                 int bit_lo, int bit_hi);
 
+// Sort 1-word keys ascending when their values are spread uniformly (mixed
+// k-mers): LSD passes over the top P = ceil(log2 n) + 8 bits only (whole
+// digits), then the rare groups of distinct keys sharing those bits are put
+// in order.  Returns true if the result is in alt.
+bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n);
+
 // ---------------------------------------------------------------- scans
 // out[i] = sum of in[0..i-1] for i in [0, n]; out has n+1 entries.
 void exclusive_scan_u64(mh_ctx* ctx, const uint64_t* in, uint64_t* out, uint64_t n);
@@ -456,9 +561,11 @@ void exclusive_scan_u32(mh_ctx* ctx, const uint32_t* in, uint64_t* out, uint64_t
 // ------------------------------------------------- counting stages
 // Sorted canonical spectrum -> solid (k+1)-mers, both strands, sorted.
 // Defined in mh_count.cu, used by mercy too (d = 1, counts looked up).
+// in_mixed: `sorted` holds mix_bij of the canonical keys (1-word keys only);
+// spec_mixed: likewise for the spectrum.
 template <int NW>
 void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, Buf<uint64_t>& out_keys,
                  Buf<uint32_t>& out_cnt, uint64_t* n_out, uint64_t* n_canon_runs, uint64_t* n_palin_runs,
-                 const uint64_t* spectrum, uint64_t n_spectrum);
+                 const uint64_t* spectrum, uint64_t n_spectrum, bool in_mixed = false, bool spec_mixed = false);
 
 }  // namespace mh

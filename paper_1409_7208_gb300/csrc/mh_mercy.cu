@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(256) mercy_probe_kernel(const uint32_t* __rest
 }
 
 // Walk from each hit to the next solid window; emit the gap if it qualifies.
-template <int NW>
+template <int NW, bool MIXED>
 __global__ void __launch_bounds__(256) mercy_walk_kernel(const uint32_t* __restrict__ packed,
                                                          const ulonglong2* __restrict__ hits, uint64_t n_hits, int k,
                                                          const Slot<NW>* __restrict__ ends, uint64_t ends_mask,
@@ -247,7 +247,9 @@ __global__ void __launch_bounds__(256) mercy_walk_kernel(const uint32_t* __restr
             if (idx >= out_cap) continue;
             Key<NW> z = load_window<NW>(packed, j, K1);
             Key<NW> rz = key_rc<NW>(z, K1);
-            store_key<NW>(out, idx, key_less<NW>(rz, z) ? rz : z);
+            Key<NW> c = key_less<NW>(rz, z) ? rz : z;
+            if constexpr (MIXED) c.w[0] = mix_bij(c.w[0]);
+            store_key<NW>(out, idx, c);
         }
     }
 }
@@ -304,14 +306,18 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
         hit_cap = n_hits;
     }
     // the gaps behind the hits
-    uint64_t out_cap = std::max<uint64_t>(1u << 20, 4 * n_hits);
+    // candidates in the spectrum's order (mixed 1-word keys), so that their
+    // sorted spectrum lookups ascend
+    const bool mixed = NW == 1 && solid->spectrum_mixed;
+    uint64_t out_cap = std::max<uint64_t>(1u << 20, 16 * n_hits);
     Buf<uint64_t> cand;
     uint64_t n_cand = 0;
     for (int attempt = 0; attempt < 2; attempt++) {
         cand = Buf<uint64_t>(ctx, out_cap * NW);
         MH_CUDA(cudaMemsetAsync(stats.p + 1, 0, sizeof(uint64_t), ctx->stream));
         if (n_hits)
-            MH_LAUNCH(ctx, "mercy_walk", grid_for(ctx, n_hits, 256, 8), 256, 0, mercy_walk_kernel<NW>, reads->packed,
+            MH_LAUNCH(ctx, "mercy_walk", grid_for(ctx, n_hits, 256, 8), 256, 0,
+                      (mixed ? mercy_walk_kernel<NW, true> : mercy_walk_kernel<NW, false>), reads->packed,
                       hits.p, n_hits, k, table.p, cap - 1, sset.p, scap - 1, cand.p, out_cap,
                       (unsigned long long*)(stats.p + 1));
         read_u64(ctx, stats.p + 1, &n_cand, 1);
@@ -322,12 +328,13 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
     sset.reset();
     table.reset();
     Buf<uint64_t> alt(ctx, (n_cand ? n_cand : 1) * NW);
-    bool in_alt = radix_sort<NW>(ctx, cand.p, alt.p, nullptr, nullptr, n_cand, 0, 2 * (k + 1));
+    bool in_alt = radix_sort<NW>(ctx, cand.p, alt.p, nullptr, nullptr, n_cand, 0, mixed ? 64 : 2 * (k + 1));
     Buf<uint64_t>& sorted = in_alt ? alt : cand;
     Buf<uint64_t> mk;
     Buf<uint32_t> mc;
     uint64_t M = 0, runs = 0, palins = 0;
-    expand_runs<NW>(ctx, sorted.p, n_cand, k, 1, mk, mc, &M, &runs, &palins, solid->spectrum, solid->n_spectrum);
+    expand_runs<NW>(ctx, sorted.p, n_cand, k, 1, mk, mc, &M, &runs, &palins, solid->spectrum, solid->n_spectrum,
+                    mixed, solid->spectrum_mixed);
     sync_and_check(ctx);
     out->k = k;
     out->nw = NW;

@@ -14,6 +14,7 @@
 // offsets of the histogram (the same for every pass); the last tile of chunk
 // c writes the digit offsets where chunk c+1 starts.
 #include <cstdlib>
+#include <vector>
 
 #include "mh_sort_kernels.cuh"
 
@@ -106,6 +107,168 @@ bool radix_sort(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint
 template bool radix_sort<1>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*, uint64_t, int, int);
 template bool radix_sort<2>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*, uint64_t, int, int);
 template bool radix_sort<4>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*, uint64_t, int, int);
+
+// ------------------------------------------------------------ spread sort
+// After LSD passes over bits [lo, 64), keys are ordered by their top bits;
+// every position whose key is below its predecessor's within a group of
+// equal top bits marks the group (once, through a bitmap of group starts),
+// and each marked group is sorted in shared memory.  Groups larger than
+// kSpreadFix keys (rare) are sorted by passes over the low bits, one
+// segment at a time.
+
+constexpr int kSpreadFix = 2048;
+
+__global__ void spread_mark_kernel(const uint64_t* __restrict__ keys, uint64_t n, int lo,
+                                   uint32_t* __restrict__ marked, uint64_t* __restrict__ list, uint64_t cap,
+                                   unsigned long long* __restrict__ count) {
+    for (uint64_t i = 1 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = keys[i], y = keys[i - 1];
+        const uint64_t px = x >> lo;
+        if (!(x < y && px == (y >> lo))) continue;
+        // first index of the group (gallop back, then bisect)
+        uint64_t hi = i - 1, step = 1, lb;
+        while (true) {
+            if (hi < step) {
+                lb = 0;
+                break;
+            }
+            if ((keys[hi - step] >> lo) != px) {
+                lb = hi - step + 1;
+                break;
+            }
+            hi -= step;
+            step <<= 1;
+        }
+        while (lb < hi) {
+            const uint64_t mid = (lb + hi) / 2;
+            if ((keys[mid] >> lo) == px) hi = mid; else lb = mid + 1;
+        }
+        const uint64_t gs = lb;
+        const uint32_t bit = 1u << (gs & 31);
+        if (atomicOr(&marked[gs >> 5], bit) & bit) continue;
+        const uint64_t slot = atomicAdd(count, 1ull);
+        if (slot < cap) list[slot] = gs;
+    }
+}
+
+__global__ void __launch_bounds__(256) spread_group_kernel(uint64_t* __restrict__ keys, uint64_t n, int lo,
+                                                           const uint64_t* __restrict__ list, uint64_t n_groups,
+                                                           ulonglong2* __restrict__ big,
+                                                           unsigned long long* __restrict__ n_big) {
+    __shared__ uint64_t sk[kSpreadFix];
+    __shared__ uint64_t s_end;
+    for (uint64_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
+        const uint64_t gs = list[g];
+        if (threadIdx.x == 0) {
+            const uint64_t px = keys[gs] >> lo;
+            uint64_t l = gs + 1, step = 1, h;
+            while (true) {  // first index with other top bits
+                const uint64_t probe = l + step - 1;
+                if (probe >= n) {
+                    h = n;
+                    break;
+                }
+                if ((keys[probe] >> lo) != px) {
+                    h = probe;
+                    break;
+                }
+                l = probe + 1;
+                step <<= 1;
+            }
+            while (l < h) {
+                const uint64_t mid = (l + h) / 2;
+                if ((keys[mid] >> lo) == px) l = mid + 1; else h = mid;
+            }
+            s_end = l;
+        }
+        __syncthreads();
+        const uint64_t size = s_end - gs;
+        if (size > (uint64_t)kSpreadFix) {
+            if (threadIdx.x == 0) big[atomicAdd(n_big, 1ull)] = make_ulonglong2(gs, s_end);
+            __syncthreads();
+            continue;
+        }
+        int p2 = 2;
+        while ((uint64_t)p2 < size) p2 <<= 1;
+        for (int i = threadIdx.x; i < p2; i += blockDim.x) sk[i] = (uint64_t)i < size ? keys[gs + i] : ~0ull;
+        __syncthreads();
+        for (int kk = 2; kk <= p2; kk <<= 1) {
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+                    const int l = i ^ j;
+                    if (l <= i) continue;
+                    const uint64_t a = sk[i], b = sk[l];
+                    if ((a > b) == ((i & kk) == 0)) {
+                        sk[i] = b;
+                        sk[l] = a;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = threadIdx.x; (uint64_t)i < size; i += blockDim.x) keys[gs + i] = sk[i];
+        __syncthreads();
+    }
+}
+
+static int ceil_log2(uint64_t n) {
+    int b = 0;
+    while (b < 64 && (1ull << b) < n) b++;
+    return b;
+}
+
+// MH_SPREAD_BITS (a multiple of 8 in [8, 64]) fixes the number of top bits
+// sorted by passes; tests use small values to run the fix-up on small inputs.
+static int spread_bits(uint64_t n) {
+    static int forced = [] {
+        const char* e = std::getenv("MH_SPREAD_BITS");
+        int v = e ? std::atoi(e) : 0;
+        return (v >= 8 && v <= 64 && v % 8 == 0) ? v : 0;
+    }();
+    return forced ? forced : ((ceil_log2(n) + 8 + 7) / 8) * 8;
+}
+
+bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n) {
+    const int P = spread_bits(n);
+    if (n <= 1 || P >= 64) return radix_sort<1>(ctx, keys, alt, nullptr, nullptr, n, 0, 64);
+    const int lo = 64 - P;
+    const bool in_alt = radix_sort<1>(ctx, keys, alt, nullptr, nullptr, n, lo, 64);
+    uint64_t* k = in_alt ? alt : keys;
+    uint64_t* other = in_alt ? keys : alt;
+    const uint64_t cap = std::max<uint64_t>(1 << 16, n / 256);
+    Buf<uint32_t> marked(ctx, ceil_div(n, 32));
+    Buf<uint64_t> list(ctx, cap), cnt(ctx, 2);
+    marked.zero();
+    cnt.zero();
+    MH_LAUNCH(ctx, "spread_fixup_mark", grid_for(ctx, n, 256), 256, 0, spread_mark_kernel, k, n, lo, marked.p, list.p,
+              cap, (unsigned long long*)cnt.p);
+    uint64_t n_groups = 0;
+    read_u64(ctx, cnt.p, &n_groups, 1);
+    if (n_groups > cap) {
+        // far more shared prefixes than uniform keys would have: sort fully
+        return in_alt != radix_sort<1>(ctx, k, other, nullptr, nullptr, n, 0, 64);
+    }
+    if (n_groups) {
+        Buf<ulonglong2> big(ctx, n_groups);
+        MH_LAUNCH(ctx, "spread_fixup_groups", (unsigned)std::min<uint64_t>(n_groups, (uint64_t)ctx->num_sms * 16), 256,
+                  0, spread_group_kernel, k, n, lo, list.p, n_groups, big.p, (unsigned long long*)(cnt.p + 1));
+        uint64_t n_big = 0;
+        read_u64(ctx, cnt.p + 1, &n_big, 1);
+        if (n_big) {
+            std::vector<ulonglong2> h(n_big);
+            MH_CUDA(cudaMemcpyAsync(h.data(), big.p, sizeof(ulonglong2) * n_big, cudaMemcpyDeviceToHost, ctx->stream));
+            sync_and_check(ctx);
+            for (const ulonglong2& seg : h) {
+                const uint64_t len = seg.y - seg.x;
+                Buf<uint64_t> tmp(ctx, len);
+                if (radix_sort<1>(ctx, k + seg.x, tmp.p, nullptr, nullptr, len, 0, lo))
+                    MH_CUDA(cudaMemcpyAsync(k + seg.x, tmp.p, len * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+            }
+        }
+    }
+    return in_alt;
+}
 
 // ------------------------------------------------------------------ scans
 constexpr int kScanThreads = 256;

@@ -176,6 +176,18 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
     // staging offset of digit d for each warp
 #pragma unroll
     for (int w = 0; w < kSortWarps; w++) warp_hist[w * 256 + d] += start;
+    __syncthreads();
+    // stage in tile digit order first: it needs no global prefix, and by the
+    // time it is done the earlier tiles have published more of theirs
+#pragma unroll
+    for (int i = 0; i < ITEMS; i++) {
+        if (full || (w0 + 32 * i < tile_n)) {
+            const uint32_t pos = wh[rd[i] & 0xFFu] + (rd[i] >> 8);
+#pragma unroll
+            for (int w = 0; w < NW; w++) stage[w * TILE + pos] = k[i].w[w];
+            if constexpr (HV) vstage[pos] = v[i];
+        }
+    }
     // look back over earlier tiles for this digit
     uint64_t excl = 0;
     if (tile > 0) {
@@ -204,17 +216,6 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
     scatter_base[d] = digit_base[d] + excl - start;
     // the chunk's last tile: where the next chunk starts writing digit d
     if (next_base && (uint64_t)(tile + 1) * TILE >= n) next_base[d] = digit_base[d] + excl + cnt;
-    __syncthreads();
-    // stage in tile digit order
-#pragma unroll
-    for (int i = 0; i < ITEMS; i++) {
-        if (full || (w0 + 32 * i < tile_n)) {
-            const uint32_t pos = wh[rd[i] & 0xFFu] + (rd[i] >> 8);
-#pragma unroll
-            for (int w = 0; w < NW; w++) stage[w * TILE + pos] = k[i].w[w];
-            if constexpr (HV) vstage[pos] = v[i];
-        }
-    }
     __syncthreads();
     // write out: consecutive staged keys of one digit go to consecutive addresses
 #pragma unroll

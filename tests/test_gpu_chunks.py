@@ -1,6 +1,9 @@
-"""The radix sort's multi-chunk path (several look-back chains per pass, digit
-offsets carried between chunks) on inputs small enough for the oracle: the
-library is run in a child process with 3 tiles per chunk."""
+"""Sort paths that only large inputs reach, run on inputs small enough for
+the oracle by a child process with a tuning variable set: the radix sort's
+multi-chunk path (several look-back chains per pass, digit offsets carried
+between chunks; 1 or 3 tiles per chunk), and the count sort's fix-up of
+keys sharing their top bits (passes over the top 8 or 16 bits only, so that
+groups are many and large)."""
 import os
 import subprocess
 import sys
@@ -33,9 +36,10 @@ print("ok")
 """ % ROOT
 
 
-@pytest.mark.parametrize("tiles", ["1", "3"])
-def test_multi_chunk_sort_matches_oracle(tiles):
-    env = dict(os.environ, MH_SORT_CHUNK_TILES=tiles)
+@pytest.mark.parametrize("var,val", [("MH_SORT_CHUNK_TILES", "1"), ("MH_SORT_CHUNK_TILES", "3"),
+                                     ("MH_SPREAD_BITS", "8"), ("MH_SPREAD_BITS", "16")])
+def test_small_input_paths_match_oracle(var, val):
+    env = dict(os.environ, **{var: val})
     p = subprocess.run([sys.executable, "-c", CHILD], env=env, capture_output=True, text=True, timeout=600)
     assert p.returncode == 0, p.stdout + p.stderr
     assert "ok" in p.stdout
