@@ -237,6 +237,16 @@ __global__ void place_pad_kernel(const uint64_t* __restrict__ own, uint64_t n_ow
     }
 }
 
+// Add a thread's 4 symbol counts to the global histogram (warp-reduced first).
+__device__ __forceinline__ void flush_hist4(const uint32_t h[4], unsigned long long* __restrict__ hist) {
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        uint32_t v = h[c];
+        for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&hist[c], (unsigned long long)v);
+    }
+}
+
 // W byte: low 4 bits W code, bit 4 last, bit 5 dummy.
 template <int NW>
 __global__ void emit_edges_kernel(const uint64_t* __restrict__ ck, const uint32_t* __restrict__ cv, uint64_t E, int K1,
@@ -253,8 +263,7 @@ __global__ void emit_edges_kernel(const uint64_t* __restrict__ ck, const uint32_
         if (mult) mult[p] = cv ? cv[i] : 0;
         h[key_sym<NW>(x, K1, 0)]++;
     }
-    for (int c = 0; c < 4; c++)
-        if (h[c]) atomicAdd(&hist[c], (unsigned long long)h[c]);
+    flush_hist4(h, hist);
 }
 
 template <int NW>
@@ -280,8 +289,7 @@ __global__ void emit_dummy_kernel(const uint64_t* __restrict__ dk, uint64_t t, i
         store_key<NW>(aux, i, key_rev<NW>(vr, k));
         h[key_sym<NW>(x, k, 0)]++;  // node symbol k-1 = v[k-2], the top symbol of x
     }
-    for (int c = 0; c < 4; c++)
-        if (h[c]) atomicAdd(&hist[c], (unsigned long long)h[c]);
+    flush_hist4(h, hist);
 }
 
 template <int NW>
@@ -296,8 +304,7 @@ __global__ void emit_dollar_kernel(const uint64_t* __restrict__ ur, uint64_t u, 
         if (mult) mult[p] = 0;
         h[key_sym<NW>(x, k, 0)]++;  // u[k-1], the top symbol of u_rev
     }
-    for (int c = 0; c < 4; c++)
-        if (h[c]) atomicAdd(&hist[c], (unsigned long long)h[c]);
+    flush_hist4(h, hist);
 }
 
 // W bytes -> W codes and the last / dummy / valid bit-vectors (warp per 32 entries).

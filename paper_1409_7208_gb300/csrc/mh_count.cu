@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(256) extract_canonical_kernel(const uint32_t* 
 // loaded to shared memory, run heads (key differs from its predecessor) are
 // marked in a bitmask, each run's end is the next head (in the tile, or the
 // first head of a later tile for the tile's last run), and the kept runs'
-// outputs are placed with a decoupled look-back over per-tile output counts.
+// outputs go to the tile's own slot of the output buffer (no dependence
+// between tiles); a scan of the per-tile counts and a copy compact them.
 
 constexpr int kRunThreads = 256;
 constexpr int kRunItems = 8;
@@ -147,10 +148,9 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
                                                            bool spec_mixed,
                                                            const uint64_t* __restrict__ next_head,
                                                            uint64_t* __restrict__ out_keys,
-                                                           uint32_t* __restrict__ out_cnt, uint64_t out_cap,
-                                                           uint64_t* __restrict__ status,
-                                                           uint32_t* __restrict__ tile_counter,
-                                                           unsigned long long* __restrict__ totals,
+                                                           uint32_t* __restrict__ out_cnt, uint32_t slot,
+                                                           uint32_t* __restrict__ tile_count,
+                                                           uint2* __restrict__ tile_stats,
                                                            uint32_t* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem[];
     // tile keys, one pad key after every 16 so that threads reading 16
@@ -158,14 +158,11 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
     uint64_t* tk = reinterpret_cast<uint64_t*>(smem);                          // [(TILE + TILE/16) * NW]
     uint32_t* head_bits = reinterpret_cast<uint32_t*>(tk + kRunTilePad * NW);  // [TILE / 32]
     uint32_t* wsum = head_bits + kRunTile / 32;                              // [8]
-    uint64_t* tile_off = reinterpret_cast<uint64_t*>(wsum + 8);             // [1]
-    uint32_t* tile_id = reinterpret_cast<uint32_t*>(tile_off + 1);          // [1] (+1 pad)
-    uint64_t* out_stage_k = reinterpret_cast<uint64_t*>(tile_id + 2);       // [TILE] if NW == 1
+    uint64_t* tile_off = reinterpret_cast<uint64_t*>(wsum + 8);             // [1] (+1 pad)
+    uint64_t* out_stage_k = tile_off + 2;                                    // [TILE] if NW == 1
     uint32_t* out_stage_c = reinterpret_cast<uint32_t*>(out_stage_k + (NW == 1 ? kRunTile : 0));  // [TILE]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) *tile_id = atomicAdd(tile_counter, 1u);
-    __syncthreads();
-    const uint64_t tile = *tile_id;
+    const uint64_t tile = blockIdx.x;
     const uint64_t start = tile * kRunTile;
     const uint32_t tn = (uint32_t)(n - start < (uint64_t)kRunTile ? n - start : (uint64_t)kRunTile);
     for (uint32_t i = tid; i < tn; i += kRunThreads) {
@@ -237,40 +234,22 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
         heads++;
         palins += palin;
     }
-    // block exclusive scan of outs
-    uint32_t x = outs;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
-        if (lane >= off) x += y;
-    }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    uint32_t wpre = 0, total = 0;
-#pragma unroll
-    for (int w = 0; w < kRunThreads / 32; w++) {
-        wpre += w < warp ? wsum[w] : 0u;
-        total += wsum[w];
-    }
-    const uint32_t excl_thread = wpre + x - outs;
-    if (warp == 0) {
-        const uint64_t excl = warp_lookback_u64(status, tile, total, err);
-        if (lane == 0) *tile_off = excl;
-    }
-    // per-tile totals of runs and palindromic runs
-    uint32_t hs = heads, ps = palins;
-    for (int off = 16; off; off >>= 1) {
-        hs += __shfl_xor_sync(0xFFFFFFFFu, hs, off);
-        ps += __shfl_xor_sync(0xFFFFFFFFu, ps, off);
-    }
-    if (lane == 0 && (hs || ps)) {
-        atomicAdd(&totals[0], (unsigned long long)hs);
-        atomicAdd(&totals[1], (unsigned long long)ps);
+    // block exclusive scan of outs; per-tile totals of runs and palindromic
+    // runs (summed by a later kernel: a shared counter would serialise on
+    // contended atomics)
+    uint32_t total, hs_tot, ps_tot;
+    const uint32_t excl_thread = block_excl_scan_256(outs, wsum, &total);
+    block_excl_scan_256(heads, wsum, &hs_tot);
+    block_excl_scan_256(palins, wsum, &ps_tot);
+    if (tid == 0) {
+        tile_stats[tile] = make_uint2(hs_tot, ps_tot);
+        tile_count[tile] = total;
+        *tile_off = tile * (uint64_t)slot;
     }
     __syncthreads();
     const uint64_t toff = *tile_off;
-    if (toff + total > out_cap) {
-        if (tid == 0 && total) atomicOr(err, ST_TABLE_FULL);
+    if (total > slot) {
+        if (tid == 0) atomicOr(err, ST_TABLE_FULL);
         return;
     }
     // a tile's outputs fill [toff, toff + total): for 1-word keys that fit,
@@ -308,12 +287,33 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
     }
 }
 
-template <int NW>
-__global__ void copy_keys_counts_kernel(const uint64_t* __restrict__ k, const uint32_t* __restrict__ c, uint64_t n,
-                                        uint64_t* __restrict__ k2, uint32_t* __restrict__ c2) {
+// totals[0] += sum of tile_stats[].x, totals[1] += sum of .y
+__global__ void sum_tile_stats_kernel(const uint2* __restrict__ st, uint64_t n, unsigned long long* __restrict__ totals) {
+    uint64_t a = 0, b = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        store_key<NW>(k2, i, load_key<NW>(k, i));
-        c2[i] = c[i];
+        a += st[i].x;
+        b += st[i].y;
+    }
+    for (int off = 16; off; off >>= 1) {
+        a += __shfl_xor_sync(0xFFFFFFFFu, a, off);
+        b += __shfl_xor_sync(0xFFFFFFFFu, b, off);
+    }
+    if ((threadIdx.x & 31) == 0 && (a || b)) {
+        atomicAdd(&totals[0], (unsigned long long)a);
+        atomicAdd(&totals[1], (unsigned long long)b);
+    }
+}
+
+// Tile t's first cnt[t] outputs (at t * slot) move to off[t].
+__global__ void runs_compact_kernel(const uint64_t* __restrict__ k, const uint32_t* __restrict__ c, uint32_t slot,
+                                    const uint32_t* __restrict__ cnt, const uint64_t* __restrict__ off,
+                                    uint64_t* __restrict__ k2, uint32_t* __restrict__ c2, int nw) {
+    const uint64_t t = blockIdx.x;
+    const uint64_t src = t * (uint64_t)slot, dst = off[t];
+    const uint32_t m = cnt[t];
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+        for (int w = 0; w < nw; w++) k2[(dst + i) * nw + w] = k[(src + i) * nw + w];
+        c2[dst + i] = c[src + i];
     }
 }
 
@@ -327,17 +327,16 @@ void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, 
     if (NW != 1 && (in_mixed || spec_mixed)) fail(MH_EUNSUPPORTED, "mixed keys are 1-word keys");
     const int K1 = k + 1;
     const uint64_t tiles = ceil_div(n ? n : 1, kRunTile);
-    // outputs: <= n when every kept run has >= 2 keys or is a palindrome (d >= 2), else <= 2n
-    const uint64_t cap = std::max<uint64_t>(1, (!spectrum && d >= 2) ? n : 2 * n);
-    Buf<uint64_t> first(ctx, tiles), next(ctx, tiles), status(ctx, tiles), totals(ctx, 2);
-    Buf<uint32_t> counter(ctx, 1);
-    Buf<uint64_t> big_k(ctx, cap * NW);
-    Buf<uint32_t> big_c(ctx, cap);
+    // a tile's outputs: <= its keys when every kept run has >= 2 keys or is a
+    // palindrome (counting with d >= 2), else <= twice its keys
+    const uint32_t slot = (!spectrum && d >= 2) ? kRunTile : 2 * kRunTile;
+    Buf<uint64_t> first(ctx, tiles), next(ctx, tiles), totals(ctx, 2), toff(ctx, tiles + 1);
+    Buf<uint32_t> tcount(ctx, tiles);
+    Buf<uint64_t> big_k(ctx, tiles * slot * NW);
+    Buf<uint32_t> big_c(ctx, tiles * slot);
     totals.zero();
     uint64_t S = 0, tot[2] = {0, 0};
     if (n) {
-        status.zero();
-        counter.zero();
         MH_LAUNCH(ctx, "runs_first_head", grid_for(ctx, tiles * 32, 256), 256, 0, run_first_head_kernel<NW>, sorted, n,
                   tiles, first.p);
         MH_LAUNCH(ctx, "runs_next_head", grid_for(ctx, tiles, 256), 256, 0, run_next_head_kernel, first.p, tiles, n,
@@ -346,13 +345,13 @@ void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, 
                             (NW == 1 ? (sizeof(uint64_t) + sizeof(uint32_t)) * kRunTile : 0);
         auto kern = in_mixed ? runs_kernel<NW, true> : runs_kernel<NW, false>;
         MH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        Buf<uint2> tstats(ctx, tiles);
         MH_LAUNCH_B(ctx, "runs", n * 8 * NW, (unsigned)tiles, kRunThreads, smem, kern, sorted, n, K1, d, spectrum,
-                    n_spectrum, spec_mixed, next.p, big_k.p, big_c.p, cap, status.p, counter.p,
-                    (unsigned long long*)totals.p, ctx->d_status);
-        // the last tile's inclusive count is the number of outputs
-        uint64_t last;
-        read_u64(ctx, status.p + (tiles - 1), &last, 1);
-        S = last & kLbCountMask;
+                    n_spectrum, spec_mixed, next.p, big_k.p, big_c.p, slot, tcount.p, tstats.p, ctx->d_status);
+        MH_LAUNCH(ctx, "runs_totals", grid_for(ctx, tiles, 256, 2), 256, 0, sum_tile_stats_kernel, tstats.p, tiles,
+                  (unsigned long long*)totals.p);
+        exclusive_scan_u32(ctx, tcount.p, toff.p, tiles);
+        read_u64(ctx, toff.p + tiles, &S, 1);
         read_u64(ctx, totals.p, tot, 2);
     }
     *n_out = S;
@@ -360,12 +359,11 @@ void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, 
     *n_palin_runs = tot[1];
     first.reset();
     next.reset();
-    status.reset();
     Buf<uint64_t> keys(ctx, (S ? S : 1) * NW), alt(ctx, (S ? S : 1) * NW);
     Buf<uint32_t> cnt(ctx, S ? S : 1), calt(ctx, S ? S : 1);
     if (S)
-        MH_LAUNCH(ctx, "runs_compact", grid_for(ctx, S, 256), 256, 0, copy_keys_counts_kernel<NW>, big_k.p, big_c.p, S,
-                  keys.p, cnt.p);
+        MH_LAUNCH(ctx, "runs_compact", (unsigned)tiles, 256, 0, runs_compact_kernel, big_k.p, big_c.p, slot, tcount.p,
+                  toff.p, keys.p, cnt.p, NW);
     big_k.reset();
     big_c.reset();
     bool in_alt = radix_sort<NW>(ctx, keys.p, alt.p, cnt.p, calt.p, S, 0, 2 * K1);

@@ -136,7 +136,43 @@ __device__ __forceinline__ uint32_t ends_find(const Slot<NW>* __restrict__ table
     return 0;
 }
 
-// Canonical solid keys into the solidity set (tags and keys, no flags).
+// Canonical solid keys into the solidity set.  1-word keys use 8-byte slots
+// holding the key itself, empty = all ones (never canonical: the reverse
+// complement of T...T is A...A, which is smaller); wider keys use Slot
+// (32-bit tag + key).
+__global__ void __launch_bounds__(256) solid_insert1_kernel(const uint64_t* __restrict__ S, uint64_t n, int K1,
+                                                            unsigned long long* __restrict__ table, uint64_t cap_mask,
+                                                            uint32_t* __restrict__ err) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        Key<1> x = load_key<1>(S, i);
+        if (key_less<1>(key_rc<1>(x, K1), x)) continue;
+        uint64_t s = key_hash<1>(x) & cap_mask;
+        bool placed = false;
+        for (uint64_t probe = 0; probe <= cap_mask; probe++) {
+            const unsigned long long prev = atomicCAS(&table[s], ~0ull, (unsigned long long)x.w[0]);
+            if (prev == ~0ull || prev == x.w[0]) {
+                placed = true;
+                break;
+            }
+            s = (s + 1) & cap_mask;
+        }
+        if (!placed) atomicOr(err, ST_TABLE_FULL);
+    }
+}
+
+__device__ __forceinline__ bool set1_has(const unsigned long long* __restrict__ table, uint64_t cap_mask, uint64_t x) {
+    Key<1> k;
+    k.w[0] = x;
+    uint64_t s = key_hash<1>(k) & cap_mask;
+    for (uint64_t probe = 0; probe <= cap_mask; probe++) {
+        const unsigned long long v = table[s];
+        if (v == x) return true;
+        if (v == ~0ull) return false;
+        s = (s + 1) & cap_mask;
+    }
+    return false;
+}
+
 template <int NW>
 __global__ void __launch_bounds__(256) solid_insert_kernel(const uint64_t* __restrict__ S, uint64_t n, int K1,
                                                            Slot<NW>* __restrict__ table, uint64_t cap_mask,
@@ -222,7 +258,7 @@ template <int NW, bool MIXED>
 __global__ void __launch_bounds__(256) mercy_walk_kernel(const uint32_t* __restrict__ packed,
                                                          const ulonglong2* __restrict__ hits, uint64_t n_hits, int k,
                                                          const Slot<NW>* __restrict__ ends, uint64_t ends_mask,
-                                                         const Slot<NW>* __restrict__ solid, uint64_t solid_mask,
+                                                         const void* __restrict__ solid, uint64_t solid_mask,
                                                          uint64_t* __restrict__ out, uint64_t out_cap,
                                                          unsigned long long* __restrict__ counter) {
     const int K1 = k + 1;
@@ -235,7 +271,13 @@ __global__ void __launch_bounds__(256) mercy_walk_kernel(const uint32_t* __restr
         for (; q < end; q++) {
             Key<NW> x = load_window<NW>(packed, q, K1);
             Key<NW> r = key_rc<NW>(x, K1);
-            if (table_has<NW>(solid, solid_mask, key_less<NW>(r, x) ? r : x)) {
+            const Key<NW> c = key_less<NW>(r, x) ? r : x;
+            bool present;
+            if constexpr (NW == 1)
+                present = set1_has(static_cast<const unsigned long long*>(solid), solid_mask, c.w[0]);
+            else
+                present = table_has<NW>(static_cast<const Slot<NW>*>(solid), solid_mask, c);
+            if (present) {
                 y = x;
                 break;
             }
@@ -285,11 +327,24 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
     flags.reset();
     // solidity set of the canonical solid keys, load <= 1/2 (<= 0.61 if all palindromes)
     const uint64_t scap = next_pow2(std::max<uint64_t>(S + S / 2, 64));
-    Buf<Slot<NW>> sset(ctx, scap);
-    sset.zero();
-    if (S)
-        MH_LAUNCH(ctx, "mercy_solid_insert", grid_for(ctx, S, 256), 256, 0, solid_insert_kernel<NW>, solid->keys, S,
-                  k + 1, sset.p, scap - 1, ctx->d_status);
+    Buf<Slot<NW>> sset;
+    Buf<unsigned long long> sset1;
+    const void* sset_p;
+    if constexpr (NW == 1) {
+        sset1 = Buf<unsigned long long>(ctx, scap);
+        MH_CUDA(cudaMemsetAsync(sset1.p, 0xFF, scap * sizeof(unsigned long long), ctx->stream));
+        if (S)
+            MH_LAUNCH(ctx, "mercy_solid_insert", grid_for(ctx, S, 256), 256, 0, solid_insert1_kernel, solid->keys, S,
+                      k + 1, sset1.p, scap - 1, ctx->d_status);
+        sset_p = sset1.p;
+    } else {
+        sset = Buf<Slot<NW>>(ctx, scap);
+        sset.zero();
+        if (S)
+            MH_LAUNCH(ctx, "mercy_solid_insert", grid_for(ctx, S, 256), 256, 0, solid_insert_kernel<NW>, solid->keys,
+                      S, k + 1, sset.p, scap - 1, ctx->d_status);
+        sset_p = sset.p;
+    }
     // windows without outdegree
     uint64_t hit_cap = std::max<uint64_t>(1u << 20, reads->n_packed / 256);
     Buf<ulonglong2> hits;
@@ -318,7 +373,7 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
         if (n_hits)
             MH_LAUNCH(ctx, "mercy_walk", grid_for(ctx, n_hits, 256, 8), 256, 0,
                       (mixed ? mercy_walk_kernel<NW, true> : mercy_walk_kernel<NW, false>), reads->packed,
-                      hits.p, n_hits, k, table.p, cap - 1, sset.p, scap - 1, cand.p, out_cap,
+                      hits.p, n_hits, k, table.p, cap - 1, sset_p, scap - 1, cand.p, out_cap,
                       (unsigned long long*)(stats.p + 1));
         read_u64(ctx, stats.p + 1, &n_cand, 1);
         if (n_cand <= out_cap) break;
@@ -326,6 +381,7 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
     }
     hits.reset();
     sset.reset();
+    sset1.reset();
     table.reset();
     Buf<uint64_t> alt(ctx, (n_cand ? n_cand : 1) * NW);
     bool in_alt = radix_sort<NW>(ctx, cand.p, alt.p, nullptr, nullptr, n_cand, 0, mixed ? 64 : 2 * (k + 1));
