@@ -151,6 +151,22 @@ class Clocks:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def job_totals(dist, device, kmers: int, edges: int, ms: float, e2e_s: float = 0.0) -> dict:
+    """Whole-job figures over all ranks: (k+1)-mers and SdBG entries are
+    summed, the timed durations take the maximum over ranks (a job ends when
+    its slowest rank does).  With dist None (one process) the local figures
+    are returned as they are."""
+    if dist is None:
+        return {"kmers": kmers, "edges": edges, "ms": ms, "e2e_s": e2e_s}
+    import torch
+    sums = torch.tensor([float(kmers), float(edges)], dtype=torch.float64, device=device)
+    maxs = torch.tensor([ms, e2e_s], dtype=torch.float64, device=device)
+    dist.all_reduce(sums, op=dist.ReduceOp.SUM)
+    dist.all_reduce(maxs, op=dist.ReduceOp.MAX)
+    return {"kmers": int(sums[0].item()), "edges": int(sums[1].item()), "ms": float(maxs[0].item()),
+            "e2e_s": float(maxs[1].item())}
+
+
 def cpu_oracle_run(ascii, offs, k, d):
     import oracle
     t0 = time.perf_counter()
@@ -265,12 +281,10 @@ def main():
     clk = clocks.stop()
     ms = t_start.elapsed_time(t_end)
     prof = ctx.profile()
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    tot = job_totals(dist, "cuda", info["n_kmers"], info["m"], ms)
+    ms = tot["ms"]
     n_kmers = info["n_kmers"]
-    value = n_kmers * world * args.steps / (ms / 1e3)
+    value = tot["kmers"] * args.steps / (ms / 1e3)
     phase_ms = {name: sum(p[i].elapsed_time(p[i + 1]) for p in phases) / len(phases)
                 for i, name in enumerate(["pack", "count", "mercy", "build"])}
 
@@ -305,11 +319,9 @@ def main():
             step(pin_ascii, pin_offs, None, download)
         torch.cuda.synchronize()
         e_s = time.perf_counter() - e0
-        if dist is not None:
-            t = torch.tensor([e_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_s = float(t.item())
-        e2e = {"value": n_kmers * world * args.e2e_steps / e_s, "unit": UNIT,
+        e_tot = job_totals(dist, "cuda", info["n_kmers"], info["m"], 0.0, e_s)
+        e_s = e_tot["e2e_s"]
+        e2e = {"value": e_tot["kmers"] * args.e2e_steps / e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(n_bases + offs.nbytes), "d2h_bytes_per_step": int(d2h["bytes"])}
 
     # roofline of the dominant kernel (radix scatter pass)
@@ -351,7 +363,7 @@ def main():
                        "per_rank": "independent read set per rank (seed + 1000 * rank)",
                        "l2": "inputs larger than L2 (%.1f GB of reads, %.1f GB of keys per step)"
                              % (n_bases / 1e9, info["n_kmers"] * 4 / 1e9)},
-            "sdbg_edges_per_s": info["m"] * world * args.steps / (ms / 1e3),
+            "sdbg_edges_per_s": tot["edges"] * args.steps / (ms / 1e3),
             "phases_ms": phase_ms,
             "sizes": {key: int(v) for key, v in info.items()},
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
