@@ -137,6 +137,7 @@ void sync_and_check(mh_ctx* ctx) {
         if (st & ST_OVERFLOW) fail(MH_EOVERFLOW, "a (k+1)-mer count exceeds 2^32-1");
         if (st & ST_TABLE_FULL) fail(MH_EDEVICE, "hash table probe sequence exhausted");
         if (st & ST_BAD_INPUT) fail(MH_EINVAL, "read offsets are not non-decreasing from 0 to n_bases");
+        if (st & ST_BAD_TABLE) fail(MH_EINVAL, "solid table is not a set of distinct sorted (k+1)-mers");
         fail(MH_EDEVICE, "device status " + std::to_string(st));
     }
 }

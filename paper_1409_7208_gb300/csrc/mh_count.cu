@@ -142,6 +142,10 @@ __device__ __forceinline__ uint64_t spectrum_count(const uint64_t* __restrict__ 
 // kept if the count is >= d.  Lookup mode: every run is kept and its count
 // is looked up in the spectrum.  A kept run outputs the key and, unless it is
 // a palindrome, its reverse complement, both with the count.
+//
+// The tile's run heads are compacted into a list (head bitmask, word prefix
+// counts), then each thread takes whole runs, so per-run work (unmixing,
+// the palindrome test, output) is not repeated for every key of a run.
 template <int NW, bool IN_MIXED>
 __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __restrict__ s, uint64_t n, int K1, int d,
                                                            const uint64_t* __restrict__ spec, uint64_t n_spec,
@@ -152,27 +156,40 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
                                                            uint32_t* __restrict__ tile_count,
                                                            uint2* __restrict__ tile_stats,
                                                            uint32_t* __restrict__ err) {
+    constexpr int kWords = kRunTile / 32;
+    constexpr int kRunsPerThread = kRunTile / kRunThreads;
     extern __shared__ __align__(16) unsigned char smem[];
-    // tile keys, one pad key after every 16 so that threads reading 16
-    // consecutive keys each hit distinct banks: key i at tk[rp(i) * NW]
+    // tile keys, one pad key after every 16 (fewer bank conflicts for
+    // threads reading keys far apart): key i at tk[rp(i) * NW]
     uint64_t* tk = reinterpret_cast<uint64_t*>(smem);                          // [(TILE + TILE/16) * NW]
     uint32_t* head_bits = reinterpret_cast<uint32_t*>(tk + kRunTilePad * NW);  // [TILE / 32]
-    uint32_t* wsum = head_bits + kRunTile / 32;                              // [8]
-    uint64_t* tile_off = reinterpret_cast<uint64_t*>(wsum + 8);             // [1] (+1 pad)
-    uint64_t* out_stage_k = tile_off + 2;                                    // [TILE] if NW == 1
+    uint32_t* wpre = head_bits + kWords;                                       // [TILE / 32 + 1] (+7 pad)
+    uint32_t* wsum = wpre + kWords + 8;                                        // [8]
+    uint16_t* hp = reinterpret_cast<uint16_t*>(wsum + 8);                      // [TILE] head positions
+    uint64_t* out_stage_k = reinterpret_cast<uint64_t*>(hp + kRunTile);        // [TILE] if NW == 1
     uint32_t* out_stage_c = reinterpret_cast<uint32_t*>(out_stage_k + (NW == 1 ? kRunTile : 0));  // [TILE]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t tile = blockIdx.x;
     const uint64_t start = tile * kRunTile;
     const uint32_t tn = (uint32_t)(n - start < (uint64_t)kRunTile ? n - start : (uint64_t)kRunTile);
-    for (uint32_t i = tid; i < tn; i += kRunThreads) {
-        Key<NW> x = load_key<NW>(s, start + i);
+    if (tn == (uint32_t)kRunTile) {
+        Key<NW> x[kRunsPerThread];
 #pragma unroll
-        for (int w = 0; w < NW; w++) tk[rp(i) * NW + w] = x.w[w];
+        for (int j = 0; j < kRunsPerThread; j++) x[j] = load_key<NW>(s, start + tid + j * kRunThreads);
+#pragma unroll
+        for (int j = 0; j < kRunsPerThread; j++)
+#pragma unroll
+            for (int w = 0; w < NW; w++) tk[rp(tid + j * kRunThreads) * NW + w] = x[j].w[w];
+    } else {
+        for (uint32_t i = tid; i < tn; i += kRunThreads) {
+            Key<NW> x = load_key<NW>(s, start + i);
+#pragma unroll
+            for (int w = 0; w < NW; w++) tk[rp(i) * NW + w] = x.w[w];
+        }
     }
     __syncthreads();
     // head bitmask, one warp per 32-key word
-    for (uint32_t wd = warp; wd < kRunTile / 32; wd += kRunThreads / 32) {
+    for (uint32_t wd = warp; wd < kWords; wd += kRunThreads / 32) {
         const uint32_t i = wd * 32 + lane;
         bool head = false;
         if (i < tn) {
@@ -191,32 +208,41 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
         if (lane == 0) head_bits[wd] = m;
     }
     __syncthreads();
-    // each thread: kRunItems consecutive keys
-    const uint32_t i0 = tid * kRunItems;
-    uint32_t outs = 0, heads = 0, palins = 0;
-    uint32_t hmask = i0 < tn ? (head_bits[i0 >> 5] >> (i0 & 31)) & ((1u << kRunItems) - 1u) : 0u;
-    uint32_t cnt[kRunItems];
-    uint8_t nout[kRunItems];
+    // heads before each word (warp 0: two words per lane)
+    static_assert(kWords == 64, "two bitmask words per lane");
+    if (warp == 0) {
+        const uint32_t c0 = __popc(head_bits[2 * lane]), c1 = __popc(head_bits[2 * lane + 1]);
+        uint32_t x = c0 + c1;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+            if (lane >= off) x += y;
+        }
+        const uint32_t ex = x - c0 - c1;
+        wpre[2 * lane] = ex;
+        wpre[2 * lane + 1] = ex + c0;
+        if (lane == 31) wpre[kWords] = x;
+    }
+    __syncthreads();
+    for (uint32_t wd = warp; wd < kWords; wd += kRunThreads / 32) {
+        const uint32_t m = head_bits[wd];
+        if ((m >> lane) & 1u) hp[wpre[wd] + __popc(m & ((1u << lane) - 1u))] = (uint16_t)(wd * 32 + lane);
+    }
+    __syncthreads();
+    const uint32_t H = wpre[kWords];
+    // thread per run: runs tid, tid + 256, ... (ascending, for the spectrum hint)
+    uint32_t cnt[kRunsPerThread];
+    uint8_t nout[kRunsPerThread];
+    uint32_t outs = 0, palins = 0;
     uint64_t hint = n_spec / 2;
 #pragma unroll
-    for (int j = 0; j < kRunItems; j++) {
+    for (int j = 0; j < kRunsPerThread; j++) {
+        const uint32_t r = tid + j * kRunThreads;
         nout[j] = 0;
         cnt[j] = 0;
-        if (!((hmask >> j) & 1u)) continue;
-        const uint32_t i = i0 + j;
-        // next head after i in this tile
-        uint64_t end = kNoHead;
-        uint32_t wd = i >> 5;
-        uint32_t m = head_bits[wd] & ~((2u << (i & 31)) - 1u);
-        while (true) {
-            if (m) {
-                end = start + wd * 32 + (uint32_t)(__ffs(m) - 1);
-                break;
-            }
-            if (++wd >= (tn + 31) / 32) break;
-            m = head_bits[wd];
-        }
-        if (end == kNoHead || end > start + tn) end = next_head[tile];
+        if (r >= H) continue;
+        const uint32_t i = hp[r];
+        const uint64_t end = r + 1 < H ? start + hp[r + 1] : next_head[tile];
         Key<NW> x;
 #pragma unroll
         for (int w = 0; w < NW; w++) x.w[w] = tk[rp(i) * NW + w];
@@ -231,36 +257,30 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
         cnt[j] = (uint32_t)c;
         if (spec || c >= (uint64_t)d) nout[j] = palin ? 1 : 2;
         outs += nout[j];
-        heads++;
         palins += palin;
     }
-    // block exclusive scan of outs; per-tile totals of runs and palindromic
-    // runs (summed by a later kernel: a shared counter would serialise on
-    // contended atomics)
-    uint32_t total, hs_tot, ps_tot;
-    const uint32_t excl_thread = block_excl_scan_256(outs, wsum, &total);
-    block_excl_scan_256(heads, wsum, &hs_tot);
-    block_excl_scan_256(palins, wsum, &ps_tot);
+    // one block scan of (outputs | palindromic runs << 16): both fit 16 bits
+    uint32_t total;
+    const uint32_t excl_thread = block_excl_scan_256(outs | (palins << 16), wsum, &total) & 0xFFFFu;
+    const uint32_t n_out = total & 0xFFFFu;
     if (tid == 0) {
-        tile_stats[tile] = make_uint2(hs_tot, ps_tot);
-        tile_count[tile] = total;
-        *tile_off = tile * (uint64_t)slot;
+        tile_stats[tile] = make_uint2(H, total >> 16);
+        tile_count[tile] = n_out;
     }
-    __syncthreads();
-    const uint64_t toff = *tile_off;
-    if (total > slot) {
+    if (n_out > slot) {
         if (tid == 0) atomicOr(err, ST_TABLE_FULL);
         return;
     }
-    // a tile's outputs fill [toff, toff + total): for 1-word keys that fit,
+    const uint64_t toff = tile * (uint64_t)slot;
+    // a tile's outputs fill [toff, toff + n_out): for 1-word keys that fit,
     // stage them in shared memory and write them out coalesced
-    const bool staged = NW == 1 && total <= (uint32_t)kRunTile;
+    const bool staged = NW == 1 && n_out <= (uint32_t)kRunTile;
     uint32_t lpos = excl_thread;
     uint64_t pos = toff + excl_thread;
 #pragma unroll
-    for (int j = 0; j < kRunItems; j++) {
+    for (int j = 0; j < kRunsPerThread; j++) {
         if (!nout[j]) continue;
-        const uint32_t i = i0 + j;
+        const uint32_t i = hp[tid + j * kRunThreads];
         Key<NW> xk;
 #pragma unroll
         for (int w = 0; w < NW; w++) xk.w[w] = tk[rp(i) * NW + w];
@@ -280,7 +300,7 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
     }
     if (staged) {
         __syncthreads();
-        for (uint32_t i = tid; i < total; i += kRunThreads) {
+        for (uint32_t i = tid; i < n_out; i += kRunThreads) {
             out_keys[toff + i] = out_stage_k[i];
             out_cnt[toff + i] = out_stage_c[i];
         }
@@ -327,9 +347,11 @@ void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, 
     if (NW != 1 && (in_mixed || spec_mixed)) fail(MH_EUNSUPPORTED, "mixed keys are 1-word keys");
     const int K1 = k + 1;
     const uint64_t tiles = ceil_div(n ? n : 1, kRunTile);
-    // a tile's outputs: <= its keys when every kept run has >= 2 keys or is a
-    // palindrome (counting with d >= 2), else <= twice its keys
-    const uint32_t slot = (!spectrum && d >= 2) ? kRunTile : 2 * kRunTile;
+    // a tile's outputs: when every kept run has >= 2 keys or is a palindrome
+    // (counting with d >= 2), the runs inside the tile give at most one
+    // output per key and the run continuing past the tile at most two
+    // (one more than its first key), so <= keys + 1; else <= twice its keys
+    const uint32_t slot = (!spectrum && d >= 2) ? kRunTile + 2 : 2 * kRunTile;
     Buf<uint64_t> first(ctx, tiles), next(ctx, tiles), totals(ctx, 2), toff(ctx, tiles + 1);
     Buf<uint32_t> tcount(ctx, tiles);
     Buf<uint64_t> big_k(ctx, tiles * slot * NW);
@@ -341,7 +363,8 @@ void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, 
                   tiles, first.p);
         MH_LAUNCH(ctx, "runs_next_head", grid_for(ctx, tiles, 256), 256, 0, run_next_head_kernel, first.p, tiles, n,
                   next.p);
-        const size_t smem = sizeof(uint64_t) * kRunTilePad * NW + sizeof(uint32_t) * (kRunTile / 32 + 8) + 16 +
+        const size_t smem = sizeof(uint64_t) * kRunTilePad * NW + sizeof(uint32_t) * (2 * (kRunTile / 32) + 16) +
+                            sizeof(uint16_t) * kRunTile +
                             (NW == 1 ? (sizeof(uint64_t) + sizeof(uint32_t)) * kRunTile : 0);
         auto kern = in_mixed ? runs_kernel<NW, true> : runs_kernel<NW, false>;
         MH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

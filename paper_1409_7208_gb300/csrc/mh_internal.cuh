@@ -26,6 +26,7 @@ constexpr uint32_t ST_SPIN_TIMEOUT = 1u;  // a bounded look-back wait gave up
 constexpr uint32_t ST_OVERFLOW = 2u;      // a count did not fit 32 bits
 constexpr uint32_t ST_TABLE_FULL = 4u;    // a hash probe sequence ran out
 constexpr uint32_t ST_BAD_INPUT = 8u;     // read offsets not monotone or out of range
+constexpr uint32_t ST_BAD_TABLE = 16u;    // a solid table with more than 4 entries per node
 
 struct Error {
     int code;

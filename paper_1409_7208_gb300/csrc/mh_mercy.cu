@@ -2,11 +2,14 @@
 //
 //   degrees  for every solid edge x (both orientations are in the sorted
 //            solid table S): out0(x) = no solid edge starts with x[1..k];
-//            in0(x) = no solid edge ends with x[0..k-1], i.e. none of
-//            c x[0..k-1] (c in ACGT) is solid.  Each thread takes 16
-//            consecutive entries of S; for entries with the same first
-//            symbol the queries ascend with x, so every lower-bound search
-//            gallops from the previous answer and stays in cache.
+//            in0(x) = no solid edge ends with x[0..k-1].  With P = the
+//            k-prefixes of S (sorted, as S is) both are a join of the
+//            suffixes x[1..k] against P: out0(x) iff x's suffix is not in P,
+//            in0(y) iff no x has y's prefix as its suffix.  S is cut into
+//            chunks of whole nodes; for each first symbol a, the entries
+//            a.s with s in the chunk's node range are a contiguous run of S
+//            (found by one search per chunk boundary), and each is looked up
+//            in the chunk's prefixes held in shared memory.
 //   ends     the edges with out0 or in0 (the graph's dead ends, a small
 //            fraction of S) go into a small open-addressing hash table with
 //            their two flags, which stays in L2.
@@ -34,44 +37,133 @@ struct Slot {
 
 __device__ __forceinline__ uint32_t slot_tag(uint64_t h) { return (uint32_t)(h >> 32) | 1u; }
 
-constexpr int kDegreeRun = 16;  // consecutive solid entries per thread
-
-// flags[i]: bit0 out0(S[i]), bit1 in0(S[i]); counts the entries with a flag.
 template <int NW>
-__global__ void __launch_bounds__(256) degree_kernel(const uint64_t* __restrict__ S, uint64_t n, int k,
-                                                     uint8_t* __restrict__ flags,
-                                                     unsigned long long* __restrict__ n_ends) {
-    uint32_t ends = 0;
-    for (uint64_t i0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) * kDegreeRun; i0 < n;
-         i0 += (uint64_t)gridDim.x * blockDim.x * kDegreeRun) {
-        uint64_t hint_out = n / 2, hint_in[4] = {n / 2, n / 2, n / 2, n / 2};
-        uint64_t i1 = i0 + kDegreeRun < n ? i0 + kDegreeRun : n;
-        for (uint64_t i = i0; i < i1; i++) {
-            Key<NW> x = load_key<NW>(S, i);
-            // out0: is there an edge x[1..k] c?  smallest candidate x[1..k] A
-            Key<NW> suf = key_low<NW>(x, 2 * k);
-            Key<NW> qo = key_shl<NW>(suf, 2);
-            uint64_t lb = gallop_lb<NW>(S, n, qo, hint_out);
-            hint_out = lb;
-            bool has_out = lb < n && key_eq<NW>(key_shr<NW>(load_key<NW>(S, lb), 2), suf);
-            // in0: is there an edge c x[0..k-1] for some c?
-            Key<NW> pre = key_shr<NW>(x, 2);
-            bool has_in = false;
+__host__ __device__ constexpr int deg_chunk() {
+    return 2048 / NW;  // entries of S per chunk (16 KB of prefixes in shared memory)
+}
+
+// First index in [0, n) with S[i] >= q.
+template <int NW>
+__device__ __forceinline__ uint64_t lb_key(const uint64_t* __restrict__ S, uint64_t n, const Key<NW>& q) {
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (key_less<NW>(load_key<NW>(S, mid), q)) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// The (k+1)-mer a followed by k symbols A (a in ACGT).
+template <int NW>
+__device__ __forceinline__ Key<NW> first_symbol_key(uint32_t a, int k) {
+    Key<NW> q = key_zero<NW>();
+    q.w[0] = a;
+    return key_shl<NW>(q, 2 * k);
+}
+
+// st[t] (t = 0..n_chunks): start of chunk t, the first node start at or after
+// t * chunk (st[n_chunks] = n).  xb[4t + a]: first entry of S that is >= a.P_t
+// where P_t is the first node of chunk t (xb[a] = start of the entries with
+// first symbol a, xb[4 n_chunks + a] = their end).
+template <int NW>
+__global__ void degree_bounds_kernel(const uint64_t* __restrict__ S, uint64_t n, int k, uint64_t n_chunks,
+                                     uint64_t* __restrict__ st, uint64_t* __restrict__ xb) {
+    constexpr int C = deg_chunk<NW>();
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < (n_chunks + 1) * 4;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t t = g >> 2;
+        const uint32_t a = (uint32_t)(g & 3);
+        uint64_t s = t == 0 ? 0 : (t == n_chunks ? n : t * C);
+        if (t > 0)
+            while (s < n && key_eq<NW>(key_shr<NW>(load_key<NW>(S, s), 2), key_shr<NW>(load_key<NW>(S, s - 1), 2)))
+                s++;
+        if (a == 0) st[t] = s;
+        uint64_t b;
+        if (t == 0) {
+            b = lb_key<NW>(S, n, first_symbol_key<NW>(a, k));
+        } else if (s >= n) {
+            b = a == 3 ? n : lb_key<NW>(S, n, first_symbol_key<NW>(a + 1, k));
+        } else {
+            Key<NW> q = first_symbol_key<NW>(a, k);
+            const Key<NW> p = key_shr<NW>(load_key<NW>(S, s), 2);
 #pragma unroll
-            for (int c = 0; c < 4; c++) {
-                Key<NW> cc = key_zero<NW>();
-                cc.w[0] = (uint64_t)c;
-                Key<NW> qi = key_shl<NW>(cc, 2 * k);
-#pragma unroll
-                for (int w = 0; w < NW; w++) qi.w[w] |= pre.w[w];
-                uint64_t li = gallop_lb<NW>(S, n, qi, hint_in[c]);
-                hint_in[c] = li;
-                has_in |= li < n && key_eq<NW>(load_key<NW>(S, li), qi);
-            }
-            uint8_t f = (has_out ? 0 : 1) | (has_in ? 0 : 2);
-            flags[i] = f;
-            ends += f != 0;
+            for (int w = 0; w < NW; w++) q.w[w] |= p.w[w];
+            b = lb_key<NW>(S, n, q);
         }
+        xb[g] = b;
+    }
+}
+
+// Block per chunk.  fout[j] = 1 iff entry j has no outdegree (for the
+// entries whose suffix falls in the chunk's node range); flags[i] = 2 iff
+// entry i of the chunk has no indegree, else 0.
+template <int NW>
+__global__ void __launch_bounds__(256) degree_kernel(const uint64_t* __restrict__ S, int k,
+                                                     const uint64_t* __restrict__ st,
+                                                     const uint64_t* __restrict__ xb, uint8_t* __restrict__ fout,
+                                                     uint8_t* __restrict__ flags, uint32_t* __restrict__ err) {
+    constexpr int C = deg_chunk<NW>();
+    constexpr int CAP = C + 4;  // a node has at most 4 entries, so a chunk at most C + 3
+    __shared__ uint64_t pk[CAP * NW];
+    __shared__ uint8_t found[CAP];
+    const uint64_t t = blockIdx.x;
+    const uint64_t p0 = st[t], p1 = st[t + 1];
+    if (p1 - p0 > (uint64_t)CAP) {
+        if (threadIdx.x == 0) atomicOr(err, ST_BAD_TABLE);
+        return;
+    }
+    const uint32_t np = (uint32_t)(p1 - p0);
+    for (uint32_t i = threadIdx.x; i < np; i += blockDim.x) {
+        const Key<NW> p = key_shr<NW>(load_key<NW>(S, p0 + i), 2);
+#pragma unroll
+        for (int w = 0; w < NW; w++) pk[i * NW + w] = p.w[w];
+        found[i] = 0;
+    }
+    __syncthreads();
+    auto pkey = [&](uint32_t i) {
+        Key<NW> r;
+#pragma unroll
+        for (int w = 0; w < NW; w++) r.w[w] = pk[i * NW + w];
+        return r;
+    };
+    for (uint32_t a = 0; a < 4; a++) {
+        const uint64_t x0 = xb[t * 4 + a], x1 = xb[(t + 1) * 4 + a];
+        for (uint64_t j = x0 + threadIdx.x; j < x1; j += blockDim.x) {
+            const Key<NW> sfx = key_low<NW>(load_key<NW>(S, j), 2 * k);
+            uint32_t lo = 0, hi = np;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (key_less<NW>(pkey(mid), sfx)) lo = mid + 1; else hi = mid;
+            }
+            const bool hit = lo < np && key_eq<NW>(pkey(lo), sfx);
+            if (hit) found[lo] = 1;
+            fout[j] = hit ? 0 : 1;
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < np; i += blockDim.x) {
+        const Key<NW> p = pkey(i);
+        uint32_t f = i;
+        while (f > 0 && key_eq<NW>(pkey(f - 1), p)) f--;
+        flags[p0 + i] = found[f] ? 0 : 2;
+    }
+}
+
+// flags[i] |= fout[i]; counts the entries with a flag.
+__global__ void degree_flags_kernel(const uint8_t* __restrict__ fout, uint8_t* __restrict__ flags, uint64_t n,
+                                    unsigned long long* __restrict__ n_ends) {
+    uint32_t ends = 0;
+    const uint64_t n4 = n / 4;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n4; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t f = reinterpret_cast<const uint32_t*>(flags)[i] | reinterpret_cast<const uint32_t*>(fout)[i];
+        reinterpret_cast<uint32_t*>(flags)[i] = f;
+        ends += ((f & 0xFFu) != 0) + ((f & 0xFF00u) != 0) + ((f & 0xFF0000u) != 0) + ((f >> 24) != 0);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < n - 4 * n4) {
+        const uint64_t i = 4 * n4 + threadIdx.x;
+        const uint8_t f = flags[i] | fout[i];
+        flags[i] = f;
+        ends += f != 0;
     }
     for (int off = 16; off; off >>= 1) ends += __shfl_xor_sync(0xFFFFFFFFu, ends, off);
     if ((threadIdx.x & 31) == 0 && ends) atomicAdd(n_ends, (unsigned long long)ends);
@@ -309,9 +401,17 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
     Buf<uint8_t> flags(ctx, S ? S : 1);
     Buf<uint64_t> stats(ctx, 2);
     stats.zero();
-    if (S)
-        MH_LAUNCH_B(ctx, "mercy_degree", S * 8 * NW, grid_for(ctx, ceil_div(S, kDegreeRun), 256), 256, 0,
-                    degree_kernel<NW>, solid->keys, S, k, flags.p, (unsigned long long*)stats.p);
+    if (S) {
+        const uint64_t n_chunks = ceil_div(S, deg_chunk<NW>());
+        Buf<uint64_t> st(ctx, n_chunks + 1), xb(ctx, 4 * (n_chunks + 1));
+        Buf<uint8_t> fout(ctx, S);
+        MH_LAUNCH(ctx, "mercy_degree_bounds", grid_for(ctx, 4 * (n_chunks + 1), 256), 256, 0,
+                  degree_bounds_kernel<NW>, solid->keys, S, k, n_chunks, st.p, xb.p);
+        MH_LAUNCH_B(ctx, "mercy_degree", 2 * S * 8 * NW + 2 * S, (unsigned)n_chunks, 256, 0, degree_kernel<NW>,
+                    solid->keys, k, st.p, xb.p, fout.p, flags.p, ctx->d_status);
+        MH_LAUNCH(ctx, "mercy_degree_flags", grid_for(ctx, ceil_div(S, 4), 256), 256, 0, degree_flags_kernel, fout.p,
+                  flags.p, S, (unsigned long long*)stats.p);
+    }
     uint64_t n_ends = 0;
     read_u64(ctx, stats.p, &n_ends, 1);
     const uint64_t cap = next_pow2(std::max<uint64_t>(2 * n_ends, 64));

@@ -43,7 +43,7 @@ static bool radix_sort_impl(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t
     // base[(p * n_chunks + c) * 256 + d]: where chunk c of pass p starts writing digit d
     Buf<uint64_t> base(ctx, (size_t)n_passes * n_chunks * 256);
     hist.zero();
-    MH_LAUNCH_B(ctx, "radix_hist", n * 8 * NW, grid_for(ctx, n, 256, 4), 256, sizeof(uint32_t) * n_passes * 256,
+    MH_LAUNCH_B(ctx, "radix_hist", n * 8 * NW, grid_for(ctx, n, 256, 8), 256, sizeof(uint32_t) * n_passes * 256,
                 radix_hist_kernel<NW>, keys, n, bit_lo, n_passes, hist.p);
     MH_LAUNCH(ctx, "radix_base", n_passes, 256, 0, radix_base_kernel, hist.p, base.p, (uint64_t)n_chunks * 256);
     const uint64_t max_tiles = std::min<uint64_t>(chunk_tiles(), ceil_div(n, TILE));
@@ -74,8 +74,9 @@ static bool radix_sort_impl(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t
 }
 
 // Tile shape of the scatter pass for 1-word keys: (items per thread,
-// resident CTAs per SM).  The default (12, 3) measured fastest on GB300;
-// MH_SORT_VARIANT selects another shape for tuning runs.
+// resident CTAs per SM).  The defaults, (12, 4) for keys alone and (12, 3)
+// with a payload (which needs more than 64 registers), measured fastest on
+// GB300; MH_SORT_VARIANT selects another key-only shape for tuning runs.
 static int sort_variant() {
     static int v = [] {
         const char* e = std::getenv("MH_SORT_VARIANT");
@@ -88,10 +89,14 @@ template <int NW, bool HV>
 static bool radix_sort_dispatch(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt,
                                 uint64_t n, int bit_lo, int bit_hi) {
     if constexpr (NW == 1) {
-        switch (sort_variant()) {
-            case 1: return radix_sort_impl<NW, HV, 16, 2>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
-            case 2: return radix_sort_impl<NW, HV, 8, 4>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
-            default: return radix_sort_impl<NW, HV, 12, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
+        if constexpr (HV) {
+            return radix_sort_impl<NW, HV, 12, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
+        } else {
+            switch (sort_variant()) {
+                case 1: return radix_sort_impl<NW, HV, 14, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
+                case 2: return radix_sort_impl<NW, HV, 12, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
+                default: return radix_sort_impl<NW, HV, 12, 4>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
+            }
         }
     }
     return radix_sort_impl<NW, HV, SortItems<NW>::v, 2>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);

@@ -50,7 +50,19 @@ __global__ void __launch_bounds__(256) radix_hist_kernel(const uint64_t* __restr
     const int nb = n_passes * 256;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
     __syncthreads();
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    // four independent loads in flight per thread before the counting
+    constexpr int U = 4;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    for (; i + (U - 1) * stride < n; i += U * stride) {
+        Key<NW> k[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) k[u] = load_key<NW>(keys, i + u * stride);
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            for (int p = 0; p < n_passes; p++) atomicAdd(&sh[p * 256 + key_digit<NW>(k[u], shift0 + 8 * p)], 1u);
+    }
+    for (; i < n; i += stride) {
         Key<NW> k = load_key<NW>(keys, i);
         for (int p = 0; p < n_passes; p++) atomicAdd(&sh[p * 256 + key_digit<NW>(k, shift0 + 8 * p)], 1u);
     }
@@ -128,8 +140,10 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
             }
         }
     }
-    // rank within the warp, stable by item then lane: the first lane of each
-    // group of equal digits adds the group size to the warp's counter
+    // rank within the warp, stable by item then lane: every lane of a group
+    // of equal digits reads the warp's counter, then the group's first lane
+    // adds the group size (the histogram is the warp's own, so plain shared
+    // loads and stores ordered by __syncwarp suffice)
     uint32_t* wh = warp_hist + warp * 256;
     const uint32_t lt_mask = (1u << lane) - 1;
 #pragma unroll
@@ -138,11 +152,11 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
         const uint32_t dg = valid ? key_digit<NW>(k[i], shift) : 256u;
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg);
         const int leader = __ffs(peers) - 1;
-        uint32_t old = 0;
-        if (lane == leader && valid) old = atomicAdd(&wh[dg], (uint32_t)__popc(peers));
-        old = __shfl_sync(0xFFFFFFFFu, old, leader);
-        rd[i] = ((old + __popc(peers & lt_mask)) << 8) | (dg & 0xFFu);
+        const uint32_t old = valid ? wh[dg] : 0u;
         __syncwarp();
+        if (lane == leader && valid) wh[dg] = old + (uint32_t)__popc(peers);
+        __syncwarp();
+        rd[i] = ((old + __popc(peers & lt_mask)) << 8) | (dg & 0xFFu);
     }
     __syncthreads();
     // per digit: exclusive prefix over warps, tile total
