@@ -334,6 +334,7 @@ void mh_free_kmers(mh_kmers* s) {
     ctx_free(s->ctx, s->keys);
     ctx_free(s->ctx, s->counts);
     ctx_free(s->ctx, s->spectrum);
+    ctx_free(s->ctx, s->canon);
     delete s;
 }
 

@@ -155,6 +155,8 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
                                                            uint32_t* __restrict__ out_cnt, uint32_t slot,
                                                            uint32_t* __restrict__ tile_count,
                                                            uint2* __restrict__ tile_stats,
+                                                           uint64_t* __restrict__ kept_slot,
+                                                           uint32_t* __restrict__ kept_count,
                                                            uint32_t* __restrict__ err) {
     constexpr int kWords = kRunTile / 32;
     constexpr int kRunsPerThread = kRunTile / kRunThreads;
@@ -165,7 +167,8 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
     uint32_t* head_bits = reinterpret_cast<uint32_t*>(tk + kRunTilePad * NW);  // [TILE / 32]
     uint32_t* wpre = head_bits + kWords;                                       // [TILE / 32 + 1] (+7 pad)
     uint32_t* wsum = wpre + kWords + 8;                                        // [8]
-    uint16_t* hp = reinterpret_cast<uint16_t*>(wsum + 8);                      // [TILE] head positions
+    uint32_t* wkept = wsum + 8;                                                // [rounds 8][warps 8]
+    uint16_t* hp = reinterpret_cast<uint16_t*>(wkept + 64);                    // [TILE] head positions
     uint64_t* out_stage_k = reinterpret_cast<uint64_t*>(hp + kRunTile);        // [TILE] if NW == 1
     uint32_t* out_stage_c = reinterpret_cast<uint32_t*>(out_stage_k + (NW == 1 ? kRunTile : 0));  // [TILE]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -259,6 +262,19 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
         outs += nout[j];
         palins += palin;
     }
+    // kept runs per warp and round (for the run-ordered kept list; read after
+    // the block scan's barriers)
+    const bool list_kept = NW == 1 && kept_slot != nullptr;
+    uint32_t kbal[kRunsPerThread];
+    if (list_kept) {
+#pragma unroll
+        for (int j = 0; j < kRunsPerThread; j++) {
+            kbal[j] = 0;
+            if ((uint32_t)(j * kRunThreads) >= H) break;
+            kbal[j] = __ballot_sync(0xFFFFFFFFu, nout[j] != 0);
+            if (lane == 0) wkept[j * 8 + warp] = __popc(kbal[j]);
+        }
+    }
     // one block scan of (outputs | palindromic runs << 16): both fit 16 bits
     uint32_t total;
     const uint32_t excl_thread = block_excl_scan_256(outs | (palins << 16), wsum, &total) & 0xFFFFu;
@@ -270,6 +286,26 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
     if (n_out > slot) {
         if (tid == 0) atomicOr(err, ST_TABLE_FULL);
         return;
+    }
+    // kept runs' input keys in run order, at the tile's own offset of
+    // kept_slot (a tile has at most as many kept runs as keys)
+    if (list_kept) {
+        uint32_t kbase = 0;
+        const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+        for (int j = 0; j < kRunsPerThread; j++) {
+            if ((uint32_t)(j * kRunThreads) >= H) break;
+            uint32_t pre = 0, tot = 0;
+#pragma unroll
+            for (int w = 0; w < kRunThreads / 32; w++) {
+                const uint32_t c = wkept[j * 8 + w];
+                pre += w < warp ? c : 0u;
+                tot += c;
+            }
+            if (nout[j]) kept_slot[start + kbase + pre + __popc(kbal[j] & lt)] = tk[rp(hp[tid + j * kRunThreads])];
+            kbase += tot;
+        }
+        if (tid == 0) kept_count[tile] = kbase;
     }
     const uint64_t toff = tile * (uint64_t)slot;
     // a tile's outputs fill [toff, toff + n_out): for 1-word keys that fit,
@@ -337,14 +373,24 @@ __global__ void runs_compact_kernel(const uint64_t* __restrict__ k, const uint32
     }
 }
 
+// Tile t's cnt[t] kept keys (at t * kRunTile) move to off[t].
+__global__ void kept_compact_kernel(const uint64_t* __restrict__ slot, const uint32_t* __restrict__ cnt,
+                                    const uint64_t* __restrict__ off, uint64_t* __restrict__ out) {
+    const uint64_t t = blockIdx.x;
+    const uint64_t src = t * (uint64_t)kRunTile, dst = off[t];
+    const uint32_t m = cnt[t];
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) out[dst + i] = slot[src + i];
+}
+
 // Sorted canonical keys -> both-strand keys of kept runs, sorted ascending.
 // spectrum == nullptr: counting mode (keep count >= d).  Otherwise every run
 // is kept with its count looked up in the spectrum.
 template <int NW>
 void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, Buf<uint64_t>& out_keys,
                  Buf<uint32_t>& out_cnt, uint64_t* n_out, uint64_t* n_canon_runs, uint64_t* n_palin_runs,
-                 const uint64_t* spectrum, uint64_t n_spectrum, bool in_mixed, bool spec_mixed) {
+                 const uint64_t* spectrum, uint64_t n_spectrum, bool in_mixed, bool spec_mixed, KeptList* kept) {
     if (NW != 1 && (in_mixed || spec_mixed)) fail(MH_EUNSUPPORTED, "mixed keys are 1-word keys");
+    if (kept && (NW != 1 || spectrum)) fail(MH_EUNSUPPORTED, "kept-run lists are for 1-word counting");
     const int K1 = k + 1;
     const uint64_t tiles = ceil_div(n ? n : 1, kRunTile);
     // a tile's outputs: when every kept run has >= 2 keys or is a palindrome
@@ -363,14 +409,26 @@ void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, 
                   tiles, first.p);
         MH_LAUNCH(ctx, "runs_next_head", grid_for(ctx, tiles, 256), 256, 0, run_next_head_kernel, first.p, tiles, n,
                   next.p);
-        const size_t smem = sizeof(uint64_t) * kRunTilePad * NW + sizeof(uint32_t) * (2 * (kRunTile / 32) + 16) +
+        const size_t smem = sizeof(uint64_t) * kRunTilePad * NW + sizeof(uint32_t) * (2 * (kRunTile / 32) + 16 + 64) +
                             sizeof(uint16_t) * kRunTile +
                             (NW == 1 ? (sizeof(uint64_t) + sizeof(uint32_t)) * kRunTile : 0);
         auto kern = in_mixed ? runs_kernel<NW, true> : runs_kernel<NW, false>;
         MH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         Buf<uint2> tstats(ctx, tiles);
+        Buf<uint32_t> kcount(ctx, kept ? tiles : 1);
         MH_LAUNCH_B(ctx, "runs", n * 8 * NW, (unsigned)tiles, kRunThreads, smem, kern, sorted, n, K1, d, spectrum,
-                    n_spectrum, spec_mixed, next.p, big_k.p, big_c.p, slot, tcount.p, tstats.p, ctx->d_status);
+                    n_spectrum, spec_mixed, next.p, big_k.p, big_c.p, slot, tcount.p, tstats.p,
+                    kept ? kept->slot.p : nullptr, kcount.p, ctx->d_status);
+        if (kept) {
+            Buf<uint64_t> koff(ctx, tiles + 1);
+            exclusive_scan_u32(ctx, kcount.p, koff.p, tiles);
+            read_u64(ctx, koff.p + tiles, &kept->n, 1);
+            kept->keys = Buf<uint64_t>(ctx, kept->n ? kept->n : 1);
+            if (kept->n)
+                MH_LAUNCH(ctx, "runs_kept_compact", (unsigned)tiles, 256, 0, kept_compact_kernel, kept->slot.p,
+                          kcount.p, koff.p, kept->keys.p);
+            kept->slot.reset();
+        }
         MH_LAUNCH(ctx, "runs_totals", grid_for(ctx, tiles, 256, 2), 256, 0, sum_tile_stats_kernel, tstats.p, tiles,
                   (unsigned long long*)totals.p);
         exclusive_scan_u32(ctx, tcount.p, toff.p, tiles);
@@ -400,11 +458,11 @@ void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, 
 }
 
 template void expand_runs<1>(mh_ctx*, const uint64_t*, uint64_t, int, int, Buf<uint64_t>&, Buf<uint32_t>&, uint64_t*,
-                             uint64_t*, uint64_t*, const uint64_t*, uint64_t, bool, bool);
+                             uint64_t*, uint64_t*, const uint64_t*, uint64_t, bool, bool, KeptList*);
 template void expand_runs<2>(mh_ctx*, const uint64_t*, uint64_t, int, int, Buf<uint64_t>&, Buf<uint32_t>&, uint64_t*,
-                             uint64_t*, uint64_t*, const uint64_t*, uint64_t, bool, bool);
+                             uint64_t*, uint64_t*, const uint64_t*, uint64_t, bool, bool, KeptList*);
 template void expand_runs<4>(mh_ctx*, const uint64_t*, uint64_t, int, int, Buf<uint64_t>&, Buf<uint32_t>&, uint64_t*,
-                             uint64_t*, uint64_t*, const uint64_t*, uint64_t, bool, bool);
+                             uint64_t*, uint64_t*, const uint64_t*, uint64_t, bool, bool, KeptList*);
 
 template <int NW>
 void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out) {
@@ -428,11 +486,17 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
     bool in_alt = kMixed ? radix_sort_spread(ctx, keys.p, alt.p, n)
                          : radix_sort<NW>(ctx, keys.p, alt.p, nullptr, nullptr, n, 0, 2 * (k + 1));
     Buf<uint64_t>& spec = in_alt ? alt : keys;
-    (in_alt ? keys : alt).reset();
+    Buf<uint64_t>& other = in_alt ? keys : alt;
     Buf<uint64_t> sk;
     Buf<uint32_t> sc;
     uint64_t S = 0, runs = 0, palins = 0;
-    expand_runs<NW>(ctx, spec.p, n, k, d, sk, sc, &S, &runs, &palins, nullptr, 0, kMixed, false);
+    // 1-word keys: the kept canonical keys (mixed, ascending) are listed too,
+    // in the free sort buffer
+    KeptList kept;
+    if (kMixed) kept.slot = std::move(other);
+    other.reset();
+    expand_runs<NW>(ctx, spec.p, n, k, d, sk, sc, &S, &runs, &palins, nullptr, 0, kMixed, false,
+                    kMixed ? &kept : nullptr);
     sync_and_check(ctx);
     out->k = k;
     out->nw = NW;
@@ -445,6 +509,10 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
     out->n_spectrum = n;
     out->spectrum_mixed = kMixed;
     out->spectrum = spec.release();
+    if (kMixed) {
+        out->n_canon = kept.n;
+        out->canon = kept.keys.release();
+    }
 }
 
 template void count_kmers<1>(mh_ctx*, const mh_reads*, int, int, mh_kmers*);

@@ -92,6 +92,10 @@ struct mh_kmers {
     uint64_t* spectrum = nullptr;
     uint64_t n_spectrum = 0;
     bool spectrum_mixed = false;  // spectrum holds mix_bij(canonical), sorted
+    // counting handles with 1-word keys: mix_bij of every solid canonical
+    // key, ascending (the solidity set of the mercy walk)
+    uint64_t* canon = nullptr;
+    uint64_t n_canon = 0;
     uint64_t n_kmers = 0, n_distinct = 0;
     mh_ctx* ctx = nullptr;
 };
@@ -564,9 +568,19 @@ void exclusive_scan_u32(mh_ctx* ctx, const uint32_t* in, uint64_t* out, uint64_t
 // Defined in mh_count.cu, used by mercy too (d = 1, counts looked up).
 // in_mixed: `sorted` holds mix_bij of the canonical keys (1-word keys only);
 // spec_mixed: likewise for the spectrum.
+// Optional output of expand_runs in counting mode (1-word keys): the kept
+// runs' input keys, in input order.  `slot` is scratch of >= n words, freed
+// once the list is compacted.
+struct KeptList {
+    Buf<uint64_t> slot;
+    Buf<uint64_t> keys;
+    uint64_t n = 0;
+};
+
 template <int NW>
 void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, Buf<uint64_t>& out_keys,
                  Buf<uint32_t>& out_cnt, uint64_t* n_out, uint64_t* n_canon_runs, uint64_t* n_palin_runs,
-                 const uint64_t* spectrum, uint64_t n_spectrum, bool in_mixed = false, bool spec_mixed = false);
+                 const uint64_t* spectrum, uint64_t n_spectrum, bool in_mixed = false, bool spec_mixed = false,
+                 KeptList* kept = nullptr);
 
 }  // namespace mh

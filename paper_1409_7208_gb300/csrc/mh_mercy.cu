@@ -18,10 +18,12 @@
 //            end), and for the few positives a probe of the small table;
 //            every window p without outdegree is recorded as a hit (its
 //            position and the end of its fragment).
-//   walk     thread per hit: step forward to the next solid window q (probes
-//            of a hash set of the canonical solid keys); if q > p+1 and q
-//            has no indegree, the windows p+1..q-1 are emitted (canonical
-//            keys).
+//   walk     thread per hit: step forward to the next solid window q; if
+//            q > p+1 and q has no indegree, the windows p+1..q-1 are emitted
+//            (canonical keys).  Solidity of 1-word keys: a search of the
+//            counting handle's solid canonical keys, ascending as mix_bij
+//            images (so evenly spread), through a bucket index on their top
+//            bits; wider keys: a hash set of the canonical solid keys.
 //   finish   sort + dedup of the candidates, counts looked up in the
 //            counting spectrum, both strands, sorted.
 #include "mh_internal.cuh"
@@ -232,35 +234,31 @@ __device__ __forceinline__ uint32_t ends_find(const Slot<NW>* __restrict__ table
 // holding the key itself, empty = all ones (never canonical: the reverse
 // complement of T...T is A...A, which is smaller); wider keys use Slot
 // (32-bit tag + key).
-__global__ void __launch_bounds__(256) solid_insert1_kernel(const uint64_t* __restrict__ S, uint64_t n, int K1,
-                                                            unsigned long long* __restrict__ table, uint64_t cap_mask,
-                                                            uint32_t* __restrict__ err) {
+// Bucket index over the ascending mixed solid keys: off[b] = first index
+// whose top `bits` bits are >= b, for b = 0..2^bits (thread per key; each
+// bucket boundary is written by exactly one thread).
+__global__ void canon_index_kernel(const uint64_t* __restrict__ canon, uint64_t n, int bits,
+                                   uint64_t* __restrict__ off) {
+    const int sh = 64 - bits;
+    const uint64_t nb = 1ull << bits;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        Key<1> x = load_key<1>(S, i);
-        if (key_less<1>(key_rc<1>(x, K1), x)) continue;
-        uint64_t s = key_hash<1>(x) & cap_mask;
-        bool placed = false;
-        for (uint64_t probe = 0; probe <= cap_mask; probe++) {
-            const unsigned long long prev = atomicCAS(&table[s], ~0ull, (unsigned long long)x.w[0]);
-            if (prev == ~0ull || prev == x.w[0]) {
-                placed = true;
-                break;
-            }
-            s = (s + 1) & cap_mask;
-        }
-        if (!placed) atomicOr(err, ST_TABLE_FULL);
+        const uint64_t b = canon[i] >> sh;
+        const uint64_t b0 = i == 0 ? 0 : (canon[i - 1] >> sh) + 1;
+        for (uint64_t x = b0; x <= b; x++) off[x] = i;
+        if (i == n - 1)
+            for (uint64_t x = b + 1; x <= nb; x++) off[x] = n;
     }
 }
 
-__device__ __forceinline__ bool set1_has(const unsigned long long* __restrict__ table, uint64_t cap_mask, uint64_t x) {
-    Key<1> k;
-    k.w[0] = x;
-    uint64_t s = key_hash<1>(k) & cap_mask;
-    for (uint64_t probe = 0; probe <= cap_mask; probe++) {
-        const unsigned long long v = table[s];
-        if (v == x) return true;
-        if (v == ~0ull) return false;
-        s = (s + 1) & cap_mask;
+// Is the mixed key m in the ascending list (bucket index off, `bits` bits)?
+__device__ __forceinline__ bool canon_has(const uint64_t* __restrict__ canon, const uint64_t* __restrict__ off,
+                                          int bits, uint64_t m) {
+    const uint64_t b = m >> (64 - bits);
+    uint64_t i = off[b];
+    const uint64_t e = off[b + 1];
+    for (; i < e; i++) {
+        const uint64_t v = canon[i];
+        if (v >= m) return v == m;
     }
     return false;
 }
@@ -346,11 +344,15 @@ __global__ void __launch_bounds__(256) mercy_probe_kernel(const uint32_t* __rest
 }
 
 // Walk from each hit to the next solid window; emit the gap if it qualifies.
+// MIXED (1-word keys): solidity from the ascending mixed solid keys `canon`
+// with its bucket index; otherwise from the hash set `solid`.
 template <int NW, bool MIXED>
 __global__ void __launch_bounds__(256) mercy_walk_kernel(const uint32_t* __restrict__ packed,
                                                          const ulonglong2* __restrict__ hits, uint64_t n_hits, int k,
                                                          const Slot<NW>* __restrict__ ends, uint64_t ends_mask,
-                                                         const void* __restrict__ solid, uint64_t solid_mask,
+                                                         const Slot<NW>* __restrict__ solid, uint64_t solid_mask,
+                                                         const uint64_t* __restrict__ canon,
+                                                         const uint64_t* __restrict__ canon_off, int canon_bits,
                                                          uint64_t* __restrict__ out, uint64_t out_cap,
                                                          unsigned long long* __restrict__ counter) {
     const int K1 = k + 1;
@@ -365,10 +367,10 @@ __global__ void __launch_bounds__(256) mercy_walk_kernel(const uint32_t* __restr
             Key<NW> r = key_rc<NW>(x, K1);
             const Key<NW> c = key_less<NW>(r, x) ? r : x;
             bool present;
-            if constexpr (NW == 1)
-                present = set1_has(static_cast<const unsigned long long*>(solid), solid_mask, c.w[0]);
+            if constexpr (MIXED)
+                present = canon_has(canon, canon_off, canon_bits, mix_bij(c.w[0]));
             else
-                present = table_has<NW>(static_cast<const Slot<NW>*>(solid), solid_mask, c);
+                present = table_has<NW>(solid, solid_mask, c);
             if (present) {
                 y = x;
                 break;
@@ -425,25 +427,29 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
         MH_LAUNCH(ctx, "mercy_ends_insert", grid_for(ctx, S, 256), 256, 0, ends_insert_kernel<NW>, solid->keys, S,
                   flags.p, table.p, cap - 1, filter.p, fbits - 1, ctx->d_status);
     flags.reset();
-    // solidity set of the canonical solid keys, load <= 1/2 (<= 0.61 if all palindromes)
-    const uint64_t scap = next_pow2(std::max<uint64_t>(S + S / 2, 64));
+    // solidity: 1-word keys use the counting handle's ascending mixed solid
+    // keys with a bucket index (4 to 8 keys a bucket); wider keys a hash set
+    // of the canonical solid keys, load <= 1/2 (<= 0.61 if all palindromes)
+    const bool mixed = NW == 1 && solid->spectrum_mixed;
+    if (mixed && !solid->canon && S) fail(MH_EINVAL, "the solid handle must come from mh_count_kmers");
     Buf<Slot<NW>> sset;
-    Buf<unsigned long long> sset1;
-    const void* sset_p;
-    if constexpr (NW == 1) {
-        sset1 = Buf<unsigned long long>(ctx, scap);
-        MH_CUDA(cudaMemsetAsync(sset1.p, 0xFF, scap * sizeof(unsigned long long), ctx->stream));
-        if (S)
-            MH_LAUNCH(ctx, "mercy_solid_insert", grid_for(ctx, S, 256), 256, 0, solid_insert1_kernel, solid->keys, S,
-                      k + 1, sset1.p, scap - 1, ctx->d_status);
-        sset_p = sset1.p;
+    uint64_t scap = 1;
+    Buf<uint64_t> canon_off;
+    int canon_bits = 1;
+    if (mixed) {
+        while (canon_bits < 40 && (2ull << canon_bits) * 4 <= solid->n_canon) canon_bits++;
+        canon_off = Buf<uint64_t>(ctx, (1ull << canon_bits) + 1);
+        canon_off.zero();
+        if (solid->n_canon)
+            MH_LAUNCH(ctx, "mercy_canon_index", grid_for(ctx, solid->n_canon, 256), 256, 0, canon_index_kernel,
+                      solid->canon, solid->n_canon, canon_bits, canon_off.p);
     } else {
+        scap = next_pow2(std::max<uint64_t>(S + S / 2, 64));
         sset = Buf<Slot<NW>>(ctx, scap);
         sset.zero();
         if (S)
             MH_LAUNCH(ctx, "mercy_solid_insert", grid_for(ctx, S, 256), 256, 0, solid_insert_kernel<NW>, solid->keys,
                       S, k + 1, sset.p, scap - 1, ctx->d_status);
-        sset_p = sset.p;
     }
     // windows without outdegree
     uint64_t hit_cap = std::max<uint64_t>(1u << 20, reads->n_packed / 256);
@@ -463,7 +469,6 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
     // the gaps behind the hits
     // candidates in the spectrum's order (mixed 1-word keys), so that their
     // sorted spectrum lookups ascend
-    const bool mixed = NW == 1 && solid->spectrum_mixed;
     uint64_t out_cap = std::max<uint64_t>(1u << 20, 16 * n_hits);
     Buf<uint64_t> cand;
     uint64_t n_cand = 0;
@@ -473,15 +478,15 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
         if (n_hits)
             MH_LAUNCH(ctx, "mercy_walk", grid_for(ctx, n_hits, 256, 8), 256, 0,
                       (mixed ? mercy_walk_kernel<NW, true> : mercy_walk_kernel<NW, false>), reads->packed,
-                      hits.p, n_hits, k, table.p, cap - 1, sset_p, scap - 1, cand.p, out_cap,
-                      (unsigned long long*)(stats.p + 1));
+                      hits.p, n_hits, k, table.p, cap - 1, sset.p, scap - 1, solid->canon, canon_off.p, canon_bits,
+                      cand.p, out_cap, (unsigned long long*)(stats.p + 1));
         read_u64(ctx, stats.p + 1, &n_cand, 1);
         if (n_cand <= out_cap) break;
         out_cap = n_cand;
     }
     hits.reset();
     sset.reset();
-    sset1.reset();
+    canon_off.reset();
     table.reset();
     Buf<uint64_t> alt(ctx, (n_cand ? n_cand : 1) * NW);
     bool in_alt = radix_sort<NW>(ctx, cand.p, alt.p, nullptr, nullptr, n_cand, 0, mixed ? 64 : 2 * (k + 1));
