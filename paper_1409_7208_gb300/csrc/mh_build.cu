@@ -3,7 +3,12 @@
 //
 //   colex     ck(e) = (e[k-1], ..., e[0], e[k]) packed, so integer order of ck
 //             is colex order of the k-prefix, then the label
-//   sort      LSD radix over ck
+//   order     no sort: solid and mercy are lex-sorted and closed under
+//             reverse complement, and for f = rc(e), ck(e) is ~f rotated by
+//             one symbol ((f[1..k] complemented, then comp f[0])).  Walking a
+//             table backwards from its end, each block of equal first symbol
+//             f[0] gives ck ascending; so the ck of solid and mercy edges are
+//             8 sorted runs, merged by a tree of merge-path merges
 //   analyse   per entry: minus flag (an earlier entry of the same group
 //             e[1..k-1] has the same label; groups are contiguous and hold at
 //             most 16 entries), node head/last flags
@@ -70,19 +75,47 @@ __device__ __forceinline__ uint64_t lb_ext(const uint64_t* __restrict__ a, uint6
     return lo;
 }
 
-// Edge keys (solid then mercy) -> colex keys, with counts as payload.
+// Colex keys of the reverse complements of the tables, read backwards:
+// out[i] = ck(rc(s[ns-1-i])) for i < ns, then the same for m; counts move
+// along as payload.  ck(rc(f)) = (~f[1..k] << 2) | comp f[0].
 template <int NW>
 __global__ void colex_kernel(const uint64_t* __restrict__ s, const uint32_t* __restrict__ sc, uint64_t ns,
                              const uint64_t* __restrict__ m, const uint32_t* __restrict__ mc, uint64_t nm, int k,
                              uint64_t* __restrict__ ck, uint32_t* __restrict__ cv) {
-    uint64_t n = ns + nm;
+    const uint64_t n = ns + nm;
+    const int K1 = k + 1;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        Key<NW> e = i < ns ? load_key<NW>(s, i) : load_key<NW>(m, i - ns);
-        Key<NW> node = key_shr<NW>(e, 2);
-        Key<NW> c = key_or_low<NW>(key_shl<NW>(key_rev<NW>(node, k), 2), e.w[0] & 3u);
+        const uint64_t src = i < ns ? ns - 1 - i : nm - 1 - (i - ns);
+        Key<NW> f = i < ns ? load_key<NW>(s, src) : load_key<NW>(m, src);
+#pragma unroll
+        for (int w = 0; w < NW; w++) f.w[w] = ~f.w[w];
+        f = key_low<NW>(f, 2 * K1);
+        const uint32_t top = (uint32_t)(key_shr<NW>(f, 2 * k).w[0] & 3u);
+        const Key<NW> c = key_or_low<NW>(key_low<NW>(key_shl<NW>(f, 2), 2 * K1), top);
         store_key<NW>(ck, i, c);
-        if (cv) cv[i] = i < ns ? sc[i] : mc[i - ns];
+        if (cv) cv[i] = i < ns ? sc[src] : mc[src];
     }
+}
+
+// bounds[3 t + c - 1] = first index of table t (0 solid, 1 mercy) whose
+// first symbol is >= c, for c = 1, 2, 3.
+template <int NW>
+__global__ void first_symbol_bounds_kernel(const uint64_t* __restrict__ s, uint64_t ns,
+                                           const uint64_t* __restrict__ m, uint64_t nm, int k,
+                                           uint64_t* __restrict__ bounds) {
+    const int t = threadIdx.x / 3, c = threadIdx.x % 3 + 1;
+    if (t >= 2) return;
+    const uint64_t* a = t == 0 ? s : m;
+    const uint64_t n = t == 0 ? ns : nm;
+    Key<NW> q = key_zero<NW>();
+    q.w[0] = (uint64_t)c;
+    q = key_shl<NW>(q, 2 * k);
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (key_less<NW>(load_key<NW>(a, mid), q)) lo = mid + 1; else hi = mid;
+    }
+    bounds[threadIdx.x] = lo;
 }
 
 // Per sorted entry: flags (bit0 minus, bit1 node head, bit2 node last in E).
@@ -346,13 +379,22 @@ void build_sdbg(mh_ctx* ctx, const mh_kmers* solid, const mh_kmers* mercy, mh_sd
         cv = Buf<uint32_t>(ctx, E ? E : 1);
         cv2 = Buf<uint32_t>(ctx, E ? E : 1);
     }
-    if (E)
+    if (E) {
+        Buf<uint64_t> fb(ctx, 6);
+        MH_LAUNCH(ctx, "first_symbol_bounds", 1, 32, 0, first_symbol_bounds_kernel<NW>, solid->keys, nS,
+                  mercy ? mercy->keys : nullptr, nM, k, fb.p);
         MH_LAUNCH(ctx, "colex_keys", grid_for(ctx, E, 256), 256, 0, colex_kernel<NW>, solid->keys, solid->counts, nS,
                   mercy ? mercy->keys : nullptr, mercy ? mercy->counts : nullptr, nM, k, ck.p,
                   want_mult ? cv.p : nullptr);
-    if (radix_sort<NW>(ctx, ck.p, ck2.p, want_mult ? cv.p : nullptr, want_mult ? cv2.p : nullptr, E, 0, 2 * K1)) {
-        std::swap(ck, ck2);
-        std::swap(cv, cv2);
+        uint64_t b[6];
+        read_u64(ctx, fb.p, b, 6);
+        // runs (label A, C, G, T) of each table: its first-symbol blocks T, G, C, A
+        const std::vector<uint64_t> runs = {0, nS - b[2], nS - b[1], nS - b[0], nS,
+                                            nS + nM - b[5], nS + nM - b[4], nS + nM - b[3], E};
+        if (merge_runs<NW>(ctx, ck.p, ck2.p, want_mult ? cv.p : nullptr, want_mult ? cv2.p : nullptr, runs)) {
+            std::swap(ck, ck2);
+            std::swap(cv, cv2);
+        }
     }
     ck2.reset();
     cv2.reset();

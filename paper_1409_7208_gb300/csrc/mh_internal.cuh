@@ -568,6 +568,12 @@ void exclusive_scan_u32(mh_ctx* ctx, const uint32_t* in, uint64_t* out, uint64_t
 // Defined in mh_count.cu, used by mercy too (d = 1, counts looked up).
 // in_mixed: `sorted` holds mix_bij of the canonical keys (1-word keys only);
 // spec_mixed: likewise for the spectrum.
+// Merge of sorted runs [bounds[i], bounds[i+1]) of keys (and payload, when
+// vals) into one sorted sequence; returns true when the result is in alt/valt.
+template <int NW>
+bool merge_runs(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt,
+                const std::vector<uint64_t>& bounds);
+
 // Optional output of expand_runs in counting mode (1-word keys): the kept
 // runs' input keys, in input order.  `slot` is scratch of >= n words, freed
 // once the list is compacted.
