@@ -93,13 +93,19 @@ def _traffic_record():
     """ncu DRAM bytes per key of the scatter pass, if recorded for the current
     kernel source."""
     path = os.path.join(ROOT, "profiles", "radix_onesweep_traffic.json")
-    src = os.path.join(ROOT, "paper_1409_7208_gb300", "csrc", "mh_sort.cu")
     try:
         rec = json.load(open(path))
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        return rec if rec.get("mh_sort_cu_sha256") == sha else None
+        return rec if rec.get("sources_sha256") == sort_sources_sha() else None
     except Exception:
         return None
+
+
+def sort_sources_sha() -> str:
+    """sha256 over the scatter pass's sources (mh_sort.cu, mh_sort_kernels.cuh)."""
+    h = hashlib.sha256()
+    for f in ("mh_sort.cu", "mh_sort_kernels.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1409_7208_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
 
 
 class Clocks:
