@@ -16,9 +16,9 @@
 //   targets   A = reversed targets (label, e[k-1], ..., e[1]) of unflagged
 //             entries; already ascending within each label, so one stable
 //             radix pass on their top 8 bits sorts them
-//   joins     zero indegree = B \ A, zero outdegree = A \ B (sorted queries
-//             in sorted arrays: each thread gallops through 8 consecutive
-//             queries); B, A and the joins are tile compactions with a
+//   joins     zero indegree = B \ A, zero outdegree = A \ B, both from one
+//             merge-path merge of A and B (an element of both has its copies
+//             adjacent in the merge); B and A are tile compactions with a
 //             decoupled look-back
 //   padding   dummy entries (node $ v[0..k-2], label v[k-1]) sorted by
 //             (v[k-2..0], v[k-1]); $ entries in the order of A \ B
@@ -164,12 +164,27 @@ __global__ void __launch_bounds__(256) nodes_targets_kernel(const uint64_t* __re
     const uint64_t tile = s_tile;
     const uint64_t i0 = tile * kCmpTile + (uint64_t)threadIdx.x * kCmpItems;
     uint32_t hm = 0, pm = 0;
+    // the 8 flags in one load, and the keys loaded before the look-back waits
+    static_assert(kCmpItems == 8, "one 8-byte flag load per thread");
+    uint8_t f8[kCmpItems];
+    if (i0 + kCmpItems <= E) {
+        const uint2 v = *reinterpret_cast<const uint2*>(fl + i0);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            f8[j] = (uint8_t)(v.x >> (8 * j));
+            f8[4 + j] = (uint8_t)(v.y >> (8 * j));
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kCmpItems; j++) f8[j] = i0 + j < E ? fl[i0 + j] : 0;
+    }
+    Key<NW> xs[kCmpItems];
 #pragma unroll
     for (int j = 0; j < kCmpItems; j++) {
         if (i0 + j < E) {
-            const uint8_t f = fl[i0 + j];
-            hm |= ((f >> 1) & 1u) << j;
-            pm |= ((f & 1u) ^ 1u) << j;
+            hm |= ((f8[j] >> 1) & 1u) << j;
+            pm |= ((f8[j] & 1u) ^ 1u) << j;
+            if ((f8[j] & 3u) != 1u) xs[j] = load_key<NW>(ck, i0 + j);
         }
     }
     uint32_t tot_b, tot_a;
@@ -188,7 +203,7 @@ __global__ void __launch_bounds__(256) nodes_targets_kernel(const uint64_t* __re
 #pragma unroll
     for (int j = 0; j < kCmpItems; j++) {
         if (!(((hm | pm) >> j) & 1u)) continue;
-        const Key<NW> x = load_key<NW>(ck, i0 + j);
+        const Key<NW> x = xs[j];
         if ((hm >> j) & 1u) store_key<NW>(B, pb++, key_shr<NW>(x, 2));
         if ((pm >> j) & 1u) {
             Key<NW> t = key_shr<NW>(x, 4);
@@ -200,46 +215,6 @@ __global__ void __launch_bounds__(256) nodes_targets_kernel(const uint64_t* __re
             store_key<NW>(A, pa++, t);
         }
     }
-}
-
-// The queries q (sorted) that are absent from the sorted array a, compacted
-// in order.  Each thread gallops through its 8 consecutive queries.
-template <int NW>
-__global__ void __launch_bounds__(256) absent_compact_kernel(const uint64_t* __restrict__ q, uint64_t nq,
-                                                             const uint64_t* __restrict__ a, uint64_t na,
-                                                             uint64_t* __restrict__ out,
-                                                             uint64_t* __restrict__ status,
-                                                             uint32_t* __restrict__ tile_counter,
-                                                             uint32_t* __restrict__ err) {
-    __shared__ uint32_t scratch[8];
-    __shared__ uint64_t off;
-    __shared__ uint32_t s_tile;
-    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
-    __syncthreads();
-    const uint64_t tile = s_tile;
-    const uint64_t i0 = tile * kCmpTile + (uint64_t)threadIdx.x * kCmpItems;
-    uint32_t am = 0;
-    uint64_t hint = na / 2;
-#pragma unroll
-    for (int j = 0; j < kCmpItems; j++) {
-        if (i0 + j < nq) {
-            const Key<NW> x = load_key<NW>(q, i0 + j);
-            const uint64_t lb = gallop_lb<NW>(a, na, x, hint);
-            hint = lb;
-            if (!(lb < na && key_eq<NW>(load_key<NW>(a, lb), x))) am |= 1u << j;
-        }
-    }
-    uint32_t tot;
-    const uint32_t e = block_excl_scan_256(__popc(am), scratch, &tot);
-    if ((threadIdx.x >> 5) == 0) {
-        const uint64_t o = warp_lookback_u64(status, tile, tot, err);
-        if ((threadIdx.x & 31) == 0) off = o;
-    }
-    __syncthreads();
-    uint64_t p = off + e;
-#pragma unroll
-    for (int j = 0; j < kCmpItems; j++)
-        if ((am >> j) & 1u) store_key<NW>(out, p++, load_key<NW>(q, i0 + j));
 }
 
 // zero-indegree reversed node v_rev -> dummy key (v[k-2], ..., v[0], v[k-1])
@@ -423,24 +398,7 @@ void build_sdbg(mh_ctx* ctx, const mh_kmers* solid, const mh_kmers* mercy, mh_sd
     // zero indegree: B \ A; zero outdegree: A \ B
     Buf<uint64_t> zin(ctx, (nB ? nB : 1) * NW), zout(ctx, (nA ? nA : 1) * NW);
     uint64_t t = 0, u = 0;
-    {
-        const uint64_t tb = ceil_div(nB ? nB : 1, kCmpTile), ta = ceil_div(nA ? nA : 1, kCmpTile);
-        Buf<uint64_t> st(ctx, tb + ta);
-        Buf<uint32_t> counter(ctx, 2);
-        st.zero();
-        counter.zero();
-        if (nB)
-            MH_LAUNCH(ctx, "absent_nodes", (unsigned)tb, 256, 0, absent_compact_kernel<NW>, B.p, nB, A.p, nA, zin.p,
-                      st.p, counter.p, ctx->d_status);
-        if (nA)
-            MH_LAUNCH(ctx, "absent_targets", (unsigned)ta, 256, 0, absent_compact_kernel<NW>, A.p, nA, B.p, nB, zout.p,
-                      st.p + tb, counter.p + 1, ctx->d_status);
-        uint64_t last[2] = {0, 0};
-        if (nB) read_u64(ctx, st.p + tb - 1, &last[0], 1);
-        if (nA) read_u64(ctx, st.p + tb + ta - 1, &last[1], 1);
-        t = last[0] & kLbCountMask;
-        u = last[1] & kLbCountMask;
-    }
+    set_differences<NW>(ctx, B.p, nB, A.p, nA, zin.p, &t, zout.p, &u);
     B.reset();
     A.reset();
     // dummy entries in colex order

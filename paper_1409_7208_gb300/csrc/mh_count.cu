@@ -367,9 +367,32 @@ __global__ void runs_compact_kernel(const uint64_t* __restrict__ k, const uint32
     const uint64_t t = blockIdx.x;
     const uint64_t src = t * (uint64_t)slot, dst = off[t];
     const uint32_t m = cnt[t];
-    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
-        for (int w = 0; w < nw; w++) k2[(dst + i) * nw + w] = k[(src + i) * nw + w];
-        c2[dst + i] = c[src + i];
+    // 8 words per thread in flight
+    for (uint32_t i0 = 0; i0 < m * nw; i0 += 8 * blockDim.x) {
+        uint64_t v[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const uint32_t i = i0 + threadIdx.x + q * blockDim.x;
+            if (i < m * nw) v[q] = k[src * nw + i];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const uint32_t i = i0 + threadIdx.x + q * blockDim.x;
+            if (i < m * nw) k2[dst * nw + i] = v[q];
+        }
+    }
+    for (uint32_t i0 = 0; i0 < m; i0 += 8 * blockDim.x) {
+        uint32_t v[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const uint32_t i = i0 + threadIdx.x + q * blockDim.x;
+            if (i < m) v[q] = c[src + i];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const uint32_t i = i0 + threadIdx.x + q * blockDim.x;
+            if (i < m) c2[dst + i] = v[q];
+        }
     }
 }
 

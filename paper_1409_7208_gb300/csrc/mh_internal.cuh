@@ -574,6 +574,11 @@ template <int NW>
 bool merge_runs(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt,
                 const std::vector<uint64_t>& bounds);
 
+// X \ Y and Y \ X of two sorted arrays without repeats, each in order.
+template <int NW>
+void set_differences(mh_ctx* ctx, const uint64_t* X, uint64_t nx, const uint64_t* Y, uint64_t ny, uint64_t* outX,
+                     uint64_t* n_outX, uint64_t* outY, uint64_t* n_outY);
+
 // Optional output of expand_runs in counting mode (1-word keys): the kept
 // runs' input keys, in input order.  `slot` is scratch of >= n words, freed
 // once the list is compacted.
