@@ -115,11 +115,25 @@ __global__ void __launch_bounds__(256) degree_kernel(const uint64_t* __restrict_
         return;
     }
     const uint32_t np = (uint32_t)(p1 - p0);
-    for (uint32_t i = threadIdx.x; i < np; i += blockDim.x) {
-        const Key<NW> p = key_shr<NW>(load_key<NW>(S, p0 + i), 2);
+    {
+        // all loads of the chunk in flight at once (blockDim.x == 256)
+        constexpr int R = (CAP + 255) / 256;
+        Key<NW> v[R];
 #pragma unroll
-        for (int w = 0; w < NW; w++) pk[i * NW + w] = p.w[w];
-        found[i] = 0;
+        for (int q = 0; q < R; q++) {
+            const uint32_t i = threadIdx.x + q * 256;
+            if (i < np) v[q] = load_key<NW>(S, p0 + i);
+        }
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+            const uint32_t i = threadIdx.x + q * 256;
+            if (i < np) {
+                const Key<NW> p = key_shr<NW>(v[q], 2);
+#pragma unroll
+                for (int w = 0; w < NW; w++) pk[i * NW + w] = p.w[w];
+                found[i] = 0;
+            }
+        }
     }
     __syncthreads();
     auto pkey = [&](uint32_t i) {

@@ -114,58 +114,176 @@ template bool radix_sort<2>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*,
 template bool radix_sort<4>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*, uint64_t, int, int);
 
 // ------------------------------------------------------------ spread sort
-// After LSD passes over bits [lo, 64), keys are ordered by their top bits;
-// every position whose key is below its predecessor's within a group of
-// equal top bits marks the group (once, through a bitmap of group starts),
-// and each marked group is sorted in shared memory.  Groups larger than
-// kSpreadFix keys (rare) are sorted by passes over the low bits, one
-// segment at a time.
+// The keys are mix_bij images, so their top bits are evenly spread: LSD
+// passes over the top P bits only (P = ceil(log2 n) rounded up to a digit)
+// leave every group of equal top bits in input order, and a group holds
+// more than one distinct key only where two keys collide on those P bits
+// (about D^2 / 2^(P+1) groups for D distinct keys).  The fix-up sorts such
+// groups.  A tile kernel reads 2048 keys (plus 256 past the tile, for the
+// group that crosses its end), finds the groups that start in the tile and
+// contain a descent, and sorts them: up to 16 keys by one thread (insertion
+// sort), larger ones by one warp (successive minima: each round finds the
+// smallest key above the previous one and its count, then writes that run).
+// Groups that do not end inside the window, or have more than 64 distinct
+// keys, go to a list for a CTA each (successive minima over the group in
+// global memory, written through the free buffer); more than 256 distinct
+// keys there (pathological) fall back to a radix sort of the segment.
 
-constexpr int kSpreadFix = 2048;
+constexpr int kFixTile = 2048;
+constexpr int kFixExt = 256;
+constexpr int kFixWin = kFixTile + kFixExt;
+constexpr int kFixWords = kFixWin / 32;
+constexpr int kFixThreadSort = 16;
+constexpr int kFixQueue = kFixWin / (kFixThreadSort + 1) + 1;  // groups of > 16 keys in a window
+constexpr int kFixWarpRounds = 64;
+constexpr int kFixBlockRounds = 256;
 
-__global__ void spread_mark_kernel(const uint64_t* __restrict__ keys, uint64_t n, int lo,
-                                   uint32_t* __restrict__ marked, uint64_t* __restrict__ list, uint64_t cap,
-                                   unsigned long long* __restrict__ count) {
-    for (uint64_t i = 1 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t x = keys[i], y = keys[i - 1];
-        const uint64_t px = x >> lo;
-        if (!(x < y && px == (y >> lo))) continue;
-        // first index of the group (gallop back, then bisect)
-        uint64_t hi = i - 1, step = 1, lb;
-        while (true) {
-            if (hi < step) {
-                lb = 0;
-                break;
-            }
-            if ((keys[hi - step] >> lo) != px) {
-                lb = hi - step + 1;
-                break;
-            }
-            hi -= step;
-            step <<= 1;
+__device__ __forceinline__ bool bit_of(const uint32_t* b, uint32_t i) { return (b[i >> 5] >> (i & 31)) & 1u; }
+
+// First set bit at or after i in b (bits [0, n)), or n.
+__device__ __forceinline__ uint32_t next_bit(const uint32_t* b, uint32_t i, uint32_t n) {
+    if (i >= n) return n;
+    uint32_t w = i >> 5;
+    uint32_t m = b[w] & ~((1u << (i & 31)) - 1u);
+    while (true) {
+        if (m) {
+            const uint32_t r = w * 32 + __ffs(m) - 1;
+            return r < n ? r : n;
         }
-        while (lb < hi) {
-            const uint64_t mid = (lb + hi) / 2;
-            if ((keys[mid] >> lo) == px) hi = mid; else lb = mid + 1;
-        }
-        const uint64_t gs = lb;
-        const uint32_t bit = 1u << (gs & 31);
-        if (atomicOr(&marked[gs >> 5], bit) & bit) continue;
-        const uint64_t slot = atomicAdd(count, 1ull);
-        if (slot < cap) list[slot] = gs;
+        if (++w * 32 >= n) return n;
+        m = b[w];
     }
 }
 
-__global__ void __launch_bounds__(256) spread_group_kernel(uint64_t* __restrict__ keys, uint64_t n, int lo,
-                                                           const uint64_t* __restrict__ list, uint64_t n_groups,
-                                                           ulonglong2* __restrict__ big,
-                                                           unsigned long long* __restrict__ n_big) {
-    __shared__ uint64_t sk[kSpreadFix];
+// Any set bit in [i, j)?
+__device__ __forceinline__ bool any_bit(const uint32_t* b, uint32_t i, uint32_t j) {
+    return next_bit(b, i, j) < j;
+}
+
+__global__ void __launch_bounds__(256) spread_fix_kernel(uint64_t* __restrict__ keys, uint64_t n, int lo,
+                                                         uint64_t* __restrict__ big, uint64_t big_cap,
+                                                         unsigned long long* __restrict__ n_big) {
+    __shared__ uint64_t K[kFixWin];
+    __shared__ uint32_t head[kFixWords], desc[kFixWords];
+    __shared__ uint32_t queue[2 * kFixQueue];  // (start, end) of the groups for warps
+    __shared__ uint32_t n_queue;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t s = blockIdx.x * (uint64_t)kFixTile;
+    const uint32_t W = (uint32_t)(n - s < (uint64_t)kFixWin ? n - s : (uint64_t)kFixWin);
+    const uint32_t len = W < (uint32_t)kFixTile ? W : (uint32_t)kFixTile;
+    const bool window_ends_array = s + W == n;
+    if (W == (uint32_t)kFixWin) {
+        // all loads in flight at once
+        uint64_t v[kFixWin / 256];
+#pragma unroll
+        for (int q = 0; q < kFixWin / 256; q++) v[q] = keys[s + tid + q * 256];
+#pragma unroll
+        for (int q = 0; q < kFixWin / 256; q++) K[tid + q * 256] = v[q];
+    } else {
+        for (uint32_t i = tid; i < W; i += 256) K[i] = keys[s + i];
+    }
+    if (tid == 0) n_queue = 0;
+    __syncthreads();
+    // a and b share their top bits iff (a ^ b) < 2^lo
+    const uint64_t same_top = 1ull << lo;
+    for (uint32_t wd = warp; wd < (uint32_t)kFixWords; wd += 8) {
+        const uint32_t i = wd * 32 + lane;
+        bool h = false, d = false;
+        if (i < W) {
+            const uint64_t x = K[i];
+            const uint64_t y = i > 0 ? K[i - 1] : (s > 0 ? keys[s - 1] : ~x);
+            h = (x ^ y) >= same_top;
+            d = i > 0 && !h && x < y;
+        }
+        const uint32_t hb = __ballot_sync(0xFFFFFFFFu, h), db = __ballot_sync(0xFFFFFFFFu, d);
+        if (lane == 0) {
+            head[wd] = hb;
+            desc[wd] = db;
+        }
+    }
+    __syncthreads();
+    // groups starting in this tile: thread per 8 positions, visiting their heads
+    uint32_t hm = tid * 8 < len ? (head[tid >> 2] >> ((tid & 3) * 8)) & 0xFFu : 0u;
+    if (tid * 8 + 8 > len) hm &= (1u << (len - tid * 8)) - 1u;
+    while (hm) {
+        const uint32_t h = tid * 8 + __ffs(hm) - 1;
+        hm &= hm - 1;
+        const uint32_t g1 = next_bit(head, h + 1, W);
+        if (g1 == W && !window_ends_array) {
+            // may run past the window: checked by a CTA of its own
+            const unsigned long long q = atomicAdd(n_big, 1ull);
+            if (q < big_cap) big[q] = s + h;
+            continue;
+        }
+        if (!any_bit(desc, h + 1, g1)) continue;
+        if (g1 - h <= (uint32_t)kFixThreadSort) {
+            for (uint32_t j = h + 1; j < g1; j++) {
+                const uint64_t x = K[j];
+                uint32_t i = j;
+                while (i > h && K[i - 1] > x) {
+                    K[i] = K[i - 1];
+                    i--;
+                }
+                K[i] = x;
+            }
+            for (uint32_t j = h; j < g1; j++) keys[s + j] = K[j];
+        } else {
+            const uint32_t q = atomicAdd(&n_queue, 1u);
+            queue[2 * q] = h;
+            queue[2 * q + 1] = g1;
+        }
+    }
+    __syncthreads();
+    // larger groups: a warp each, by successive minima, from K to keys
+    const uint32_t nq = n_queue;
+    for (uint32_t q = warp; q < nq; q += 8) {
+        const uint32_t g0 = queue[2 * q], g1 = queue[2 * q + 1];
+        uint32_t pos = g0;
+        uint64_t prev = 0;
+        bool first = true;
+        int rounds = 0;
+        while (pos < g1 && rounds < kFixWarpRounds) {
+            // smallest key above prev, and its count
+            uint64_t mn = ~0ull;
+            for (uint32_t i = g0 + lane; i < g1; i += 32) {
+                const uint64_t x = K[i];
+                if ((first || x > prev) && x < mn) mn = x;
+            }
+            for (int off = 16; off; off >>= 1) {
+                const uint64_t o = __shfl_xor_sync(0xFFFFFFFFu, mn, off);
+                mn = o < mn ? o : mn;
+            }
+            uint32_t c = 0;
+            for (uint32_t i = g0 + lane; i < g1; i += 32) c += K[i] == mn;
+            for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, off);
+            for (uint32_t i = lane; i < c; i += 32) keys[s + pos + i] = mn;
+            pos += c;
+            prev = mn;
+            first = false;
+            rounds++;
+        }
+        if (pos < g1 && lane == 0) {
+            // too many distinct keys: rewrite the group as it was and defer it
+            for (uint32_t i = g0; i < g1; i++) keys[s + i] = K[i];
+            const unsigned long long b = atomicAdd(n_big, 1ull);
+            if (b < big_cap) big[b] = s + g0;
+        }
+    }
+}
+
+// A CTA per listed group start: find the group's end, skip it if sorted,
+// else sort it by successive minima through tmp (the free buffer).
+__global__ void __launch_bounds__(256) spread_big_kernel(uint64_t* __restrict__ keys, uint64_t* __restrict__ tmp,
+                                                         uint64_t n, int lo, const uint64_t* __restrict__ list,
+                                                         uint64_t n_list, ulonglong2* __restrict__ rest,
+                                                         unsigned long long* __restrict__ n_rest) {
     __shared__ uint64_t s_end;
-    for (uint64_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
+    __shared__ uint64_t red64[8];
+    __shared__ uint32_t red32[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (uint64_t g = blockIdx.x; g < n_list; g += gridDim.x) {
         const uint64_t gs = list[g];
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             const uint64_t px = keys[gs] >> lo;
             uint64_t l = gs + 1, step = 1, h;
             while (true) {  // first index with other top bits
@@ -188,31 +306,49 @@ __global__ void __launch_bounds__(256) spread_group_kernel(uint64_t* __restrict_
             s_end = l;
         }
         __syncthreads();
-        const uint64_t size = s_end - gs;
-        if (size > (uint64_t)kSpreadFix) {
-            if (threadIdx.x == 0) big[atomicAdd(n_big, 1ull)] = make_ulonglong2(gs, s_end);
-            __syncthreads();
-            continue;
-        }
-        int p2 = 2;
-        while ((uint64_t)p2 < size) p2 <<= 1;
-        for (int i = threadIdx.x; i < p2; i += blockDim.x) sk[i] = (uint64_t)i < size ? keys[gs + i] : ~0ull;
-        __syncthreads();
-        for (int kk = 2; kk <= p2; kk <<= 1) {
-            for (int j = kk >> 1; j > 0; j >>= 1) {
-                for (int i = threadIdx.x; i < p2; i += blockDim.x) {
-                    const int l = i ^ j;
-                    if (l <= i) continue;
-                    const uint64_t a = sk[i], b = sk[l];
-                    if ((a > b) == ((i & kk) == 0)) {
-                        sk[i] = b;
-                        sk[l] = a;
-                    }
-                }
-                __syncthreads();
+        const uint64_t ge = s_end;
+        // sorted already?
+        uint32_t d = 0;
+        for (uint64_t i = gs + 1 + tid; i < ge; i += 256) d |= keys[i] < keys[i - 1];
+        d = __syncthreads_or(d);
+        if (!d) continue;
+        uint64_t pos = gs, prev = 0;
+        bool first = true;
+        int rounds = 0;
+        while (pos < ge && rounds < kFixBlockRounds) {
+            uint64_t mn = ~0ull;
+            uint32_t c = 0;
+            for (uint64_t i = gs + tid; i < ge; i += 256) {
+                const uint64_t x = keys[i];
+                if ((first || x > prev) && x < mn) mn = x;
             }
+            for (int off = 16; off; off >>= 1) {
+                const uint64_t o = __shfl_xor_sync(0xFFFFFFFFu, mn, off);
+                mn = o < mn ? o : mn;
+            }
+            if (lane == 0) red64[warp] = mn;
+            __syncthreads();
+            mn = red64[0];
+            for (int w = 1; w < 8; w++) mn = red64[w] < mn ? red64[w] : mn;
+            for (uint64_t i = gs + tid; i < ge; i += 256) c += keys[i] == mn;
+            for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, off);
+            __syncthreads();
+            if (lane == 0) red32[warp] = c;
+            __syncthreads();
+            c = 0;
+            for (int w = 0; w < 8; w++) c += red32[w];
+            for (uint64_t i = tid; i < c; i += 256) tmp[pos + i] = mn;
+            pos += c;
+            prev = mn;
+            first = false;
+            rounds++;
+            __syncthreads();
         }
-        for (int i = threadIdx.x; (uint64_t)i < size; i += blockDim.x) keys[gs + i] = sk[i];
+        if (pos < ge) {
+            if (tid == 0) rest[atomicAdd(n_rest, 1ull)] = make_ulonglong2(gs, ge);
+        } else {
+            for (uint64_t i = gs + tid; i < ge; i += 256) keys[i] = tmp[i];
+        }
         __syncthreads();
     }
 }
@@ -231,7 +367,7 @@ static int spread_bits(uint64_t n) {
         int v = e ? std::atoi(e) : 0;
         return (v >= 8 && v <= 64 && v % 8 == 0) ? v : 0;
     }();
-    return forced ? forced : ((ceil_log2(n) + 8 + 7) / 8) * 8;
+    return forced ? forced : std::max(8, ((ceil_log2(n) + 7) / 8) * 8);
 }
 
 bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n) {
@@ -241,34 +377,32 @@ bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n) {
     const bool in_alt = radix_sort<1>(ctx, keys, alt, nullptr, nullptr, n, lo, 64);
     uint64_t* k = in_alt ? alt : keys;
     uint64_t* other = in_alt ? keys : alt;
-    const uint64_t cap = std::max<uint64_t>(1 << 16, n / 256);
-    Buf<uint32_t> marked(ctx, ceil_div(n, 32));
+    const uint64_t cap = std::max<uint64_t>(1 << 16, n / 64);
     Buf<uint64_t> list(ctx, cap), cnt(ctx, 2);
-    marked.zero();
     cnt.zero();
-    MH_LAUNCH(ctx, "spread_fixup_mark", grid_for(ctx, n, 256), 256, 0, spread_mark_kernel, k, n, lo, marked.p, list.p,
-              cap, (unsigned long long*)cnt.p);
-    uint64_t n_groups = 0;
-    read_u64(ctx, cnt.p, &n_groups, 1);
-    if (n_groups > cap) {
-        // far more shared prefixes than uniform keys would have: sort fully
+    MH_LAUNCH_B(ctx, "spread_fixup", n * 8, (unsigned)ceil_div(n, kFixTile), 256, 0, spread_fix_kernel, k, n, lo,
+                list.p, cap, (unsigned long long*)cnt.p);
+    uint64_t n_big = 0;
+    read_u64(ctx, cnt.p, &n_big, 1);
+    if (n_big > cap) {
+        // far more long or crowded groups than evenly spread keys give: sort fully
         return in_alt != radix_sort<1>(ctx, k, other, nullptr, nullptr, n, 0, 64);
     }
-    if (n_groups) {
-        Buf<ulonglong2> big(ctx, n_groups);
-        MH_LAUNCH(ctx, "spread_fixup_groups", (unsigned)std::min<uint64_t>(n_groups, (uint64_t)ctx->num_sms * 16), 256,
-                  0, spread_group_kernel, k, n, lo, list.p, n_groups, big.p, (unsigned long long*)(cnt.p + 1));
-        uint64_t n_big = 0;
-        read_u64(ctx, cnt.p + 1, &n_big, 1);
-        if (n_big) {
-            std::vector<ulonglong2> h(n_big);
-            MH_CUDA(cudaMemcpyAsync(h.data(), big.p, sizeof(ulonglong2) * n_big, cudaMemcpyDeviceToHost, ctx->stream));
+    if (n_big) {
+        Buf<ulonglong2> rest(ctx, n_big);
+        MH_LAUNCH(ctx, "spread_fixup_big", (unsigned)std::min<uint64_t>(n_big, (uint64_t)ctx->num_sms * 8), 256, 0,
+                  spread_big_kernel, k, other, n, lo, list.p, n_big, rest.p, (unsigned long long*)(cnt.p + 1));
+        uint64_t n_rest = 0;
+        read_u64(ctx, cnt.p + 1, &n_rest, 1);
+        if (n_rest) {
+            std::vector<ulonglong2> h(n_rest);
+            MH_CUDA(cudaMemcpyAsync(h.data(), rest.p, sizeof(ulonglong2) * n_rest, cudaMemcpyDeviceToHost,
+                                    ctx->stream));
             sync_and_check(ctx);
             for (const ulonglong2& seg : h) {
                 const uint64_t len = seg.y - seg.x;
-                Buf<uint64_t> tmp(ctx, len);
-                if (radix_sort<1>(ctx, k + seg.x, tmp.p, nullptr, nullptr, len, 0, lo))
-                    MH_CUDA(cudaMemcpyAsync(k + seg.x, tmp.p, len * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+                if (radix_sort<1>(ctx, k + seg.x, other + seg.x, nullptr, nullptr, len, 0, lo))
+                    MH_CUDA(cudaMemcpyAsync(k + seg.x, other + seg.x, len * 8, cudaMemcpyDeviceToDevice, ctx->stream));
             }
         }
     }
