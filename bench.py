@@ -101,10 +101,9 @@ def _traffic_record():
 
 
 def sort_sources_sha() -> str:
-    """sha256 over the scatter pass's sources (mh_sort.cu, mh_sort_kernels.cuh)."""
+    """sha256 of the scatter pass's kernel source (mh_sort_kernels.cuh)."""
     h = hashlib.sha256()
-    for f in ("mh_sort.cu", "mh_sort_kernels.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1409_7208_gb300", "csrc", f), "rb").read())
+    h.update(open(os.path.join(ROOT, "paper_1409_7208_gb300", "csrc", "mh_sort_kernels.cuh"), "rb").read())
     return h.hexdigest()
 
 
