@@ -75,6 +75,7 @@ typedef struct mh_ctx mh_ctx;
 typedef struct mh_reads mh_reads;
 typedef struct mh_kmers mh_kmers;
 typedef struct mh_sdbg mh_sdbg;
+typedef struct mh_contigs mh_contigs;
 
 /* Allocator callbacks.  alloc returns device memory of at least `bytes`
  * bytes, usable in stream order on `stream`, or NULL on failure; free returns
@@ -190,6 +191,46 @@ typedef struct {
 } mh_sdbg_view;
 int mh_sdbg_view_get(const mh_sdbg* g, mh_sdbg_view* v);
 void mh_free_sdbg(mh_sdbg* g);
+
+/* ------------------------------------------- multiple-k iteration */
+
+/* The paper (Sec. 2 fourth paragraph, Sec. 3) builds the graph for a list of
+ * increasing k and carries the contigs of each k into the graph of the next.
+ * Graph cleaning and contig assembly are outside this library; a contig here
+ * is a random walk of the graph E = solid + mercy (mercy may be NULL):
+ *   r(w, j)   SplitMix64 output number (w << 24) + j of the stream seeded
+ *             with `seed` (state advanced by 0x9E3779B97F4A7C15, output
+ *             z ^= z >> 30, z *= 0xBF58476D1CE4E5B9, z ^= z >> 27,
+ *             z *= 0x94D049BB133111EB, z ^= z >> 31);
+ *   walk w    starts at edge r(w, 0) mod |E| of solid followed by mercy (each
+ *             in ascending order), its k+1 symbols; step j = 1, 2, ... takes
+ *             the out-edges of the walk's last k symbols (the edges of E with
+ *             that k-prefix) in label order, stops if there are none, else
+ *             appends the label of out-edge r(w, j) mod (their number); a
+ *             walk stops at max_len symbols.
+ * Contig w is walk w (n_walks contigs, none if E is empty), as ACGT bytes.
+ * k + 1 <= max_len < 2^24, n_walks < 2^40.  Errors: MH_EINVAL, MH_ENOMEM,
+ * MH_EDEVICE. */
+int mh_walk_contigs(mh_ctx* ctx, const mh_kmers* solid, const mh_kmers* mercy, uint64_t n_walks, uint64_t max_len,
+                    uint64_t seed, mh_contigs** out);
+
+typedef struct {
+    int k;                    /* the graph's k */
+    uint64_t n;               /* contigs */
+    uint64_t n_bases;         /* bases of all contigs */
+    const uint8_t* ascii;     /* device, n_bases bytes, 'A' 'C' 'G' 'T' */
+    const uint64_t* offs;     /* device, n + 1 offsets into ascii */
+} mh_contigs_view;
+int mh_contigs_view_get(const mh_contigs* c, mh_contigs_view* v);
+void mh_free_contigs(mh_contigs* c);
+
+/* mh_pack_reads on device buffers, with `copies` copies of every contig of
+ * `contigs` (may be NULL) appended as reads: copy c of contig i is read
+ * n_reads + i * copies + c.  With copies = d every (k'+1)-mer of a contig is
+ * solid at the next k' (the contig-derived edges).  Errors: as
+ * mh_pack_reads. */
+int mh_pack_reads_contigs(mh_ctx* ctx, const uint8_t* ascii, uint64_t n_bases, const uint64_t* offs,
+                          uint64_t n_reads, const mh_contigs* contigs, int copies, mh_reads** out);
 
 /* ------------------------------------------------- no-allocation sort */
 

@@ -34,7 +34,8 @@ SYMBOLS = (
     "mh_count_kmers", "mh_mercy_kmers", "mh_kmers_view_get", "mh_free_kmers", "mh_build_sdbg",
     "mh_sdbg_view_get", "mh_free_sdbg", "mh_strerror", "mh_last_error_message", "mh_stream",
     "mh_memory", "mh_profile_count", "mh_profile_get", "mh_profile_reset", "mh_set_profile",
-    "mh_sort_keys_noalloc",
+    "mh_sort_keys_noalloc", "mh_walk_contigs", "mh_contigs_view_get", "mh_free_contigs",
+    "mh_pack_reads_contigs",
 )
 
 
@@ -70,6 +71,11 @@ class SdbgView(ctypes.Structure):
                 ("u", ctypes.c_uint64), ("n_nodes", ctypes.c_uint64), ("F", ctypes.c_uint64 * 6),
                 ("W", ctypes.c_void_p), ("last", ctypes.c_void_p), ("valid", ctypes.c_void_p),
                 ("dummy", ctypes.c_void_p), ("aux", ctypes.c_void_p), ("mult", ctypes.c_void_p)]
+
+
+class ContigsView(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("n", ctypes.c_uint64), ("n_bases", ctypes.c_uint64),
+                ("ascii", ctypes.c_void_p), ("offs", ctypes.c_void_p)]
 
 
 _lib = None
@@ -111,6 +117,10 @@ def load_library(path: str = LIB_PATH):
     lib.mh_profile_reset.argtypes = [P]
     lib.mh_set_profile.argtypes = [P, ctypes.c_int]
     lib.mh_sort_keys_noalloc.argtypes = [P, P, u64, ctypes.c_int, ctypes.c_int, P]
+    lib.mh_walk_contigs.argtypes = [P, P, P, u64, u64, u64, PP]
+    lib.mh_contigs_view_get.argtypes = [P, ctypes.POINTER(ContigsView)]
+    lib.mh_free_contigs.argtypes = [P]
+    lib.mh_pack_reads_contigs.argtypes = [P, P, u64, P, u64, P, ctypes.c_int, PP]
     _lib = lib
     return lib
 
@@ -345,6 +355,31 @@ class Sdbg(_Handle):
         return out
 
 
+class Contigs(_Handle):
+    _free_name = "mh_free_contigs"
+
+    def view(self) -> ContigsView:
+        v = ContigsView()
+        self.ctx._check(self.ctx._lib.mh_contigs_view_get(self._h, ctypes.byref(v)))
+        return v
+
+    def tensors(self) -> dict:
+        v = self.view()
+        d = self.ctx.device
+        return {"k": v.k, "n": v.n, "n_bases": v.n_bases,
+                "ascii": _tensor(v.ascii, (v.n_bases,), "|u1", self, d),
+                "offs": _tensor(v.offs, (v.n + 1,), "<i8", self, d)}
+
+    def numpy(self) -> dict:
+        t = self.tensors()
+        return {"k": t["k"], "ascii": t["ascii"].cpu().numpy(), "offs": t["offs"].cpu().numpy().view(np.uint64)}
+
+    def strings(self) -> list:
+        c = self.numpy()
+        a, o = c["ascii"].tobytes(), c["offs"]
+        return [a[int(o[i]):int(o[i + 1])].decode() for i in range(len(o) - 1)]
+
+
 # ------------------------------------------------------- the C entry points
 
 def _ptr_of(x):
@@ -395,6 +430,30 @@ def mh_build_sdbg(ctx: Context, solid: Kmers, mercy: Kmers | None = None) -> Sdb
     ctx._check(ctx._lib.mh_build_sdbg(ctx._h, solid._h, mercy._h if mercy is not None else None,
                                       ctypes.byref(h)))
     return Sdbg(ctx, h)
+
+
+def mh_walk_contigs(ctx: Context, solid: Kmers, mercy: Kmers | None, n_walks: int, max_len: int,
+                    seed: int) -> Contigs:
+    """Contigs as seeded random walks of the graph solid + mercy."""
+    h = ctypes.c_void_p()
+    ctx._check(ctx._lib.mh_walk_contigs(ctx._h, solid._h, mercy._h if mercy is not None else None, int(n_walks),
+                                        int(max_len), int(seed), ctypes.byref(h)))
+    return Contigs(ctx, h)
+
+
+def mh_pack_reads_contigs(ctx: Context, ascii, offs, contigs: Contigs | None, copies: int) -> Reads:
+    """mh_pack_reads of device reads plus ``copies`` copies of every contig."""
+    pa, da = _ptr_of(ascii)
+    po, do = _ptr_of(offs)
+    if not (da and do):
+        raise ValueError("ascii and offs must be device tensors")
+    n_bases = int(ascii.shape[0])
+    n_reads = int(offs.shape[0]) - 1
+    h = ctypes.c_void_p()
+    ctx._check(ctx._lib.mh_pack_reads_contigs(ctx._h, pa if n_bases else None, n_bases, po, n_reads,
+                                              contigs._h if contigs is not None else None, int(copies),
+                                              ctypes.byref(h)))
+    return Reads(ctx, h)
 
 
 def mh_sort_keys_noalloc(keys_in, keys_out, nw: int, key_bits: int, stream=None) -> None:

@@ -258,6 +258,58 @@ int mh_pack_reads(mh_ctx* ctx, const uint8_t* ascii, uint64_t n_bases, const uin
     });
 }
 
+int mh_pack_reads_contigs(mh_ctx* ctx, const uint8_t* ascii, uint64_t n_bases, const uint64_t* offs,
+                          uint64_t n_reads, const mh_contigs* contigs, int copies, mh_reads** out) {
+    if (!ctx || !out || !offs || (!ascii && n_bases) || copies < 0) return MH_EINVAL;
+    *out = nullptr;
+    return guarded(ctx, [&] {
+        MH_CUDA(cudaSetDevice(ctx->device));
+        auto r = std::make_unique<mh_reads>();
+        r->ctx = ctx;
+        pack_with_contigs(ctx, ascii, n_bases, offs, n_reads, contigs, (uint32_t)copies, r.get());
+        *out = r.release();
+    });
+}
+
+int mh_walk_contigs(mh_ctx* ctx, const mh_kmers* solid, const mh_kmers* mercy, uint64_t n_walks, uint64_t max_len,
+                    uint64_t seed, mh_contigs** out) {
+    if (!ctx || !solid || !out) return MH_EINVAL;
+    *out = nullptr;
+    if ((mercy && mercy->k != solid->k) || max_len < (uint64_t)solid->k + 1 || max_len >= (1ull << 24) ||
+        n_walks >= (1ull << 40)) {
+        ctx->last_error = "mh_walk_contigs: need k+1 <= max_len < 2^24, n_walks < 2^40, equal k";
+        return MH_EINVAL;
+    }
+    return guarded(ctx, [&] {
+        MH_CUDA(cudaSetDevice(ctx->device));
+        auto c = std::make_unique<mh_contigs>();
+        c->ctx = ctx;
+        switch (solid->nw) {
+            case 1: walk_contigs<1>(ctx, solid, mercy, n_walks, (uint32_t)max_len, seed, c.get()); break;
+            case 2: walk_contigs<2>(ctx, solid, mercy, n_walks, (uint32_t)max_len, seed, c.get()); break;
+            default: walk_contigs<4>(ctx, solid, mercy, n_walks, (uint32_t)max_len, seed, c.get()); break;
+        }
+        *out = c.release();
+    });
+}
+
+int mh_contigs_view_get(const mh_contigs* c, mh_contigs_view* v) {
+    if (!c || !v) return MH_EINVAL;
+    v->k = c->k;
+    v->n = c->n;
+    v->n_bases = c->n_bases;
+    v->ascii = c->ascii;
+    v->offs = c->offs;
+    return MH_OK;
+}
+
+void mh_free_contigs(mh_contigs* c) {
+    if (!c) return;
+    ctx_free(c->ctx, c->ascii);
+    ctx_free(c->ctx, c->offs);
+    delete c;
+}
+
 int mh_reads_view_get(const mh_reads* r, mh_reads_view* v) {
     if (!r || !v) return MH_EINVAL;
     v->n_reads = r->n_reads;

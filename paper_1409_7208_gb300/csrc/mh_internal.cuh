@@ -100,6 +100,14 @@ struct mh_kmers {
     mh_ctx* ctx = nullptr;
 };
 
+struct mh_contigs {
+    int k = 0;
+    uint64_t n = 0, n_bases = 0;
+    uint8_t* ascii = nullptr;   // n_bases (+16) bytes, ACGT
+    uint64_t* offs = nullptr;   // n + 1
+    mh_ctx* ctx = nullptr;
+};
+
 struct mh_sdbg {
     int k = 0, nw = 1;
     uint64_t m = 0, t = 0, u = 0, n_nodes = 0;
@@ -578,6 +586,12 @@ bool merge_runs(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint
 template <int NW>
 void set_differences(mh_ctx* ctx, const uint64_t* X, uint64_t nx, const uint64_t* Y, uint64_t ny, uint64_t* outX,
                      uint64_t* n_outX, uint64_t* outY, uint64_t* n_outY);
+
+template <int NW>
+void walk_contigs(mh_ctx* ctx, const mh_kmers* solid, const mh_kmers* mercy, uint64_t n_walks, uint32_t max_len,
+                  uint64_t seed, mh_contigs* out);
+void pack_with_contigs(mh_ctx* ctx, const uint8_t* d_ascii, uint64_t n_bases, const uint64_t* d_offs,
+                       uint64_t n_reads, const mh_contigs* contigs, uint32_t copies, mh_reads* out);
 
 // Optional output of expand_runs in counting mode (1-word keys): the kept
 // runs' input keys, in input order.  `slot` is scratch of >= n words, freed
