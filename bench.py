@@ -65,11 +65,12 @@ def _args():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="metagenome", choices=sorted(WORKLOADS))
+    p.add_argument("--workload", default="metagenome", choices=sorted(WORKLOADS) + ["multik"])
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--pairs", type=int, default=10_000_000,
-                   help="read pairs of the metagenome workload (smaller values: profiling cases only)")
+    p.add_argument("--pairs", type=int, default=None,
+                   help="read pairs (default: 10M for metagenome, 20M for multik; smaller values: "
+                        "profiling and test cases only)")
     return p.parse_args()
 
 
@@ -204,10 +205,153 @@ def run_reference(args, wl, rank, world):
     print(json.dumps(line), flush=True)
 
 
+MULTIK = {
+    "name": "multiple-k iteration: uniform genome at 20x (200 Mbp for 20M pairs), read pairs as single-end "
+            "100 bp reads, 1% iid errors, k in {27,47,67,87,99}, d=2; per k 16384 contig walks of <= 10 kbp, "
+            "carried into the next k as d copies each",
+    "ks": (27, 47, 67, 87, 99), "d": 2, "seed": 3, "walks": 16384, "max_len": 10_000,
+}
+
+
+def _multik_reads(seed, pairs):
+    import synth
+    n_reads = 2 * pairs
+    return synth.uniform_genome_reads(seed, n_reads * 100 // 20, n_reads, 100, 0.01)
+
+
+def _multik_oracle(ascii, offs):
+    from oracle import walk as ow
+    t0 = time.perf_counter()
+    steps = ow.iterate(ascii, offs, MULTIK["ks"], MULTIK["d"], 64, 500, MULTIK["seed"])
+    return sum(st["counts"]["n_kmers"] for st in steps), time.perf_counter() - t0
+
+
+def run_multik(args, rank, world, local):
+    """One step = the whole iteration over MULTIK's k list (count, mercy, SdBG
+    and contig walks per k); value = (k+1)-mers of all k per second."""
+    import numpy as np
+    import torch
+
+    import paper_1409_7208_gb300 as mh
+    from paper_1409_7208_gb300 import multik
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pairs = args.pairs or 20_000_000
+    ascii, offs = _multik_reads(MULTIK["seed"] + 1000 * rank, pairs)
+    # one stream for torch and the library: the launching stream of every
+    # kernel, on which every timing event is recorded
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
+    ctx = mh.Context(device=local, stream=stream)
+    d_ascii = torch.from_numpy(ascii).cuda()
+    d_offs = torch.from_numpy(offs.view(np.int64)).cuda()
+    ks, d = MULTIK["ks"], MULTIK["d"]
+
+    def step(a, o):
+        return multik.iterate(ctx, a, o, ks, d, MULTIK["walks"], MULTIK["max_len"], MULTIK["seed"])
+
+    for _ in range(args.warmup):
+        sizes = step(d_ascii, d_offs)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    ctx.profile_reset()
+    ctx.set_profile(True)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        sizes = step(d_ascii, d_offs)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ctx.set_profile(False)
+    clk = clocks.stop()
+    n_kmers = sum(st["n_kmers"] for st in sizes)
+    n_edges = sum(st["m"] for st in sizes)
+    tot = job_totals(dist, "cuda", n_kmers, n_edges, t0.elapsed_time(t1))
+    ms = tot["ms"]
+    prof = ctx.profile()
+    e2e = None
+    if args.e2e_steps > 0:
+        pin_a = torch.from_numpy(ascii).pin_memory()
+        pin_o = torch.from_numpy(offs.view(np.int64)).pin_memory()
+        torch.cuda.synchronize()
+        e0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            a = pin_a.to("cuda", non_blocking=True)
+            o = pin_o.to("cuda", non_blocking=True)
+            res = multik.iterate(ctx, a, o, ks, d, MULTIK["walks"], MULTIK["max_len"], MULTIK["seed"],
+                                 keep=False)
+            torch.cuda.synchronize()
+        e_s = job_totals(dist, "cuda", n_kmers, n_edges, 0.0, time.perf_counter() - e0)["e2e_s"]
+        e2e = {"value": tot["kmers"] * args.e2e_steps / e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(ascii.nbytes + offs.nbytes),
+               "d2h_bytes_per_step": 8 * 7 * len(res),
+               "note": "the per-k sizes come back to the host; the graphs stay on the device"}
+    peak, peak_kind = _peak_hbm()
+    launches, o_ms, o_bytes = prof.get("radix_onesweep", (0, 0.0, 0))
+    achieved = o_bytes / (o_ms / 1e3) / 1e9 if o_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": "radix_onesweep", "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "launches": launches}
+    kernels = {name: {"launches": la, "ms_per_step": t / args.steps}
+               for name, (la, t, b) in sorted(prof.items(), key=lambda kv: -kv[1][1])[:12]}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sa, so = _multik_reads(MULTIK["seed"], 2000)
+        n_s, t_s = _multik_oracle(sa, so)
+        cpu = {"value": n_s / t_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "4000 reads of the generator (genome 20 kbp), walks 64 x <= 500 bp, %d (k+1)-mers "
+                         "over the k list, %.1f s" % (n_s, t_s)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": tot["kmers"] * args.steps / (ms / 1e3), "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                "data": "synthetic",
+                "config": {"workload": MULTIK["name"], "reads": len(offs) - 1, "bases": len(ascii),
+                           "ks": list(ks), "d": d, "walks": MULTIK["walks"], "max_len": MULTIK["max_len"],
+                           "l2": "inputs larger than L2 (%.1f GB of reads)" % (len(ascii) / 1e9)},
+                "sdbg_edges_per_s": tot["edges"] * args.steps / (ms / 1e3),
+                "per_k": sizes, "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": sum(la for (la, _, _) in prof.values()), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     args = _args()
-    wl = WORKLOADS[args.workload]
     rank, world, local = _dist()
+    if args.workload == "multik":
+        if args.impl == "reference":
+            if rank == 0:
+                sa, so = _multik_reads(MULTIK["seed"], 2000)
+                for _ in range(args.warmup):
+                    _multik_oracle(sa, so)
+                n_s = t_s = 0
+                for _ in range(args.steps):
+                    n, t = _multik_oracle(sa, so)
+                    n_s += n
+                    t_s += t
+                v = n_s / t_s
+                print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+                                  "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                                  "ms_per_step": 1e3 * t_s / args.steps, "higher_is_better": True,
+                                  "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                                  "config": {"workload": MULTIK["name"], "sample_reads": len(so) - 1},
+                                  "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                                   "sample": "4000 reads, walks 64 x <= 500 bp"},
+                                  "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                          "d2h_bytes_per_step": 0}}), flush=True)
+            return
+        return run_multik(args, rank, world, local)
+    wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl, rank, world)
 
@@ -227,9 +371,12 @@ def main():
             dist.barrier()
 
     k, d = wl["k"], wl["d"]
-    ascii, offs = wl["gen"](wl["seed"] + 1000 * rank, args.pairs)
+    ascii, offs = wl["gen"](wl["seed"] + 1000 * rank, args.pairs or 10_000_000)
     n_bases = len(ascii)
-    stream = torch.cuda.current_stream()
+    # one stream for torch and the library: the launching stream of every
+    # kernel, on which every timing event is recorded
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
     ctx = mh.Context(device=local, stream=stream)
     d_ascii = torch.from_numpy(ascii).cuda()
     d_offs = torch.from_numpy(offs.view(np.int64)).cuda()
@@ -302,15 +449,16 @@ def main():
     def download(g):
         t = g.tensors()
         nbytes = 0
-        for key in ("W", "last", "valid", "dummy", "aux"):
-            src = t[key]
-            buf = host_bufs.get(key)
-            if buf is None or buf.numel() < src.numel():
-                buf = torch.empty(max(1, src.numel()), dtype=src.dtype, pin_memory=True)
-                host_bufs[key] = buf
-            if src.numel():
-                buf[: src.numel()].view(src.shape).copy_(src, non_blocking=True)
-            nbytes += src.numel() * src.element_size()
+        with torch.cuda.stream(stream):  # copies in order behind the library's work
+            for key in ("W", "last", "valid", "dummy", "aux"):
+                src = t[key]
+                buf = host_bufs.get(key)
+                if buf is None or buf.numel() < src.numel():
+                    buf = torch.empty(max(1, src.numel()), dtype=src.dtype, pin_memory=True)
+                    host_bufs[key] = buf
+                if src.numel():
+                    buf[: src.numel()].view(src.shape).copy_(src, non_blocking=True)
+                nbytes += src.numel() * src.element_size()
         stream.synchronize()
         d2h["bytes"] = nbytes + 48  # + F, returned by value
 

@@ -85,7 +85,8 @@ typedef void (*mh_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
 
 typedef struct {
     int device;            /* CUDA device ordinal */
-    void* stream;          /* cudaStream_t to run on; NULL = a stream the context creates */
+    void* stream;          /* cudaStream_t to run on; NULL = a blocking stream the context
+                              creates (ordered with the legacy default stream) */
     uint64_t hbm_budget;   /* max bytes the context may hold at once; 0 = no limit */
     mh_alloc_fn alloc;     /* NULL = the library's stream-ordered pool */
     mh_free_fn free;       /* must be set iff alloc is set */

@@ -208,6 +208,14 @@ class Context:
     def handle(self):
         return self._h
 
+    def stream(self):
+        """The library's stream as a torch stream (record timing events on it)."""
+        import torch
+        ptr = self._lib.mh_stream(self._h)
+        if ptr == self.torch_stream.cuda_stream:
+            return self.torch_stream
+        return torch.cuda.ExternalStream(ptr, device=self.device)
+
     def memory(self):
         a, b = ctypes.c_uint64(), ctypes.c_uint64()
         self._lib.mh_memory(self._h, ctypes.byref(a), ctypes.byref(b))

@@ -183,7 +183,9 @@ int mh_create(const mh_config* cfg, mh_ctx** out) {
         if (cfg->stream) {
             ctx->stream = (cudaStream_t)cfg->stream;
         } else {
-            MH_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+            // a blocking stream: ordered with the legacy default stream, as a
+            // caller on that stream expects
+            MH_CUDA(cudaStreamCreate(&ctx->stream));
             ctx->own_stream = true;
         }
         ctx->alloc = cfg->alloc;
