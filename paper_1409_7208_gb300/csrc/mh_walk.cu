@@ -17,9 +17,13 @@
 //            also stops at max_len symbols.
 //
 // A thread runs one walk: each step is one lower-bound search per table
-// (node.A) and a look at the next 4 entries, so the walk needs no index
-// beyond the sorted tables.  Walks write into fixed slots of max_len bytes,
-// compacted afterwards.
+// (node.A) and a look at the next 4 entries.  The search starts from a
+// bucket index of each table over the top bits of its keys (about 16 keys a
+// bucket), so a step costs a few dependent loads instead of a search of the
+// whole table.  Walks write into fixed slots of max_len bytes, compacted
+// afterwards.
+#include <algorithm>
+
 #include "mh_internal.cuh"
 
 namespace mh {
@@ -31,12 +35,36 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t c) {
     return z ^ (z >> 31);
 }
 
+// Top `bits` bits of a (k+1)-mer key (bits <= 2(k+1), bits <= 32).
+template <int NW>
+__device__ __forceinline__ uint64_t top_bits(const Key<NW>& x, int K1, int bits) {
+    return key_shr<NW>(x, 2 * K1 - bits).w[0];
+}
+
+// off[b] = first entry of the sorted table whose top bits are >= b, for
+// b = 0 .. 2^bits (thread per entry; each boundary written by one thread).
+template <int NW>
+__global__ void table_index_kernel(const uint64_t* __restrict__ T, uint64_t n, int K1, int bits,
+                                   uint64_t* __restrict__ off) {
+    const uint64_t nb = 1ull << bits;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t b = top_bits<NW>(load_key<NW>(T, i), K1, bits);
+        const uint64_t b0 = i == 0 ? 0 : top_bits<NW>(load_key<NW>(T, i - 1), K1, bits) + 1;
+        for (uint64_t x = b0; x <= b; x++) off[x] = i;
+        if (i == n - 1)
+            for (uint64_t x = b + 1; x <= nb; x++) off[x] = n;
+    }
+}
+
 // Labels (bit c for label c) of the entries of a sorted table with k-prefix v.
 template <int NW>
-__device__ __forceinline__ uint32_t out_labels(const uint64_t* __restrict__ T, uint64_t n, const Key<NW>& v) {
+__device__ __forceinline__ uint32_t out_labels(const uint64_t* __restrict__ T, uint64_t n,
+                                               const uint64_t* __restrict__ off, int K1, int bits,
+                                               const Key<NW>& v) {
     if (!n) return 0;
     const Key<NW> q = key_shl<NW>(v, 2);
-    uint64_t lo = 0, hi = n;
+    const uint64_t b = top_bits<NW>(q, K1, bits);
+    uint64_t lo = off[b], hi = off[b + 1];
     while (lo < hi) {
         const uint64_t mid = (lo + hi) >> 1;
         if (key_less<NW>(load_key<NW>(T, mid), q)) lo = mid + 1; else hi = mid;
@@ -51,9 +79,10 @@ __device__ __forceinline__ uint32_t out_labels(const uint64_t* __restrict__ T, u
 }
 
 template <int NW>
-__global__ void walk_kernel(const uint64_t* __restrict__ S, uint64_t nS, const uint64_t* __restrict__ M, uint64_t nM,
-                            int k, uint64_t n_walks, uint32_t max_len, uint64_t seed, uint8_t* __restrict__ slots,
-                            uint64_t* __restrict__ lens) {
+__global__ void walk_kernel(const uint64_t* __restrict__ S, uint64_t nS, const uint64_t* __restrict__ offS,
+                            const uint64_t* __restrict__ M, uint64_t nM, const uint64_t* __restrict__ offM,
+                            int bits, int k, uint64_t n_walks, uint32_t max_len, uint64_t seed,
+                            uint8_t* __restrict__ slots, uint64_t* __restrict__ lens) {
     const int K1 = k + 1;
     const uint64_t E = nS + nM;
     for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < n_walks;
@@ -65,7 +94,7 @@ __global__ void walk_kernel(const uint64_t* __restrict__ S, uint64_t nS, const u
         uint32_t len = K1;
         for (uint32_t j = 1; len < max_len; j++) {
             const Key<NW> v = key_low<NW>(x, 2 * k);
-            const uint32_t mask = out_labels<NW>(S, nS, v) | out_labels<NW>(M, nM, v);
+            const uint32_t mask = out_labels<NW>(S, nS, offS, K1, bits, v) | out_labels<NW>(M, nM, offM, K1, bits, v);
             if (!mask) break;
             uint32_t r = (uint32_t)(splitmix64_at(seed, (w << 24) + j) % (uint64_t)__popc(mask));
             uint32_t m = mask;
@@ -95,9 +124,22 @@ void walk_contigs(mh_ctx* ctx, const mh_kmers* solid, const mh_kmers* mercy, uin
     if (nS + nM == 0) n_walks = 0;
     Buf<uint8_t> slots(ctx, n_walks * max_len);
     Buf<uint64_t> lens(ctx, n_walks + 1), off(ctx, n_walks + 1);
-    if (n_walks)
-        MH_LAUNCH(ctx, "walk", grid_for(ctx, n_walks, 128), 128, 0, walk_kernel<NW>, solid->keys, nS,
-                  mercy ? mercy->keys : nullptr, nM, k, n_walks, max_len, seed, slots.p, lens.p);
+    // bucket indexes over the top bits: about 16 entries a bucket
+    int bits = 1;
+    while (bits < 32 && bits < 2 * (k + 1) && (2ull << bits) * 16 <= std::max(nS, nM)) bits++;
+    Buf<uint64_t> offS(ctx, (1ull << bits) + 1), offM(ctx, (1ull << bits) + 1);
+    offS.zero();
+    offM.zero();
+    if (n_walks) {
+        if (nS)
+            MH_LAUNCH(ctx, "walk_index", grid_for(ctx, nS, 256), 256, 0, table_index_kernel<NW>, solid->keys, nS,
+                      k + 1, bits, offS.p);
+        if (nM)
+            MH_LAUNCH(ctx, "walk_index", grid_for(ctx, nM, 256), 256, 0, table_index_kernel<NW>, mercy->keys, nM,
+                      k + 1, bits, offM.p);
+        MH_LAUNCH(ctx, "walk", grid_for(ctx, n_walks, 128), 128, 0, walk_kernel<NW>, solid->keys, nS, offS.p,
+                  mercy ? mercy->keys : nullptr, nM, offM.p, bits, k, n_walks, max_len, seed, slots.p, lens.p);
+    }
     exclusive_scan_u64(ctx, lens.p, off.p, n_walks);
     uint64_t total = 0;
     read_u64(ctx, off.p + n_walks, &total, 1);
