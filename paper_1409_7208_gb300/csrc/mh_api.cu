@@ -27,6 +27,7 @@ void cuda_check(cudaError_t e, const char* what) {
 void* ctx_alloc(mh_ctx* ctx, size_t bytes) {
     if (bytes == 0) bytes = 1;
     bytes = (bytes + 255) & ~size_t(255);
+    std::lock_guard<std::mutex> lock(ctx->alloc_mu);
     if (ctx->budget && ctx->in_use + bytes > ctx->budget)
         fail(MH_ENOMEM, "HBM budget exceeded: " + std::to_string(ctx->in_use) + " + " + std::to_string(bytes) +
                             " > " + std::to_string(ctx->budget) + " bytes");
@@ -50,6 +51,7 @@ void* ctx_alloc(mh_ctx* ctx, size_t bytes) {
 
 void ctx_free(mh_ctx* ctx, void* p) {
     if (!p) return;
+    std::lock_guard<std::mutex> lock(ctx->alloc_mu);
     auto it = ctx->sizes.find(p);
     size_t bytes = it == ctx->sizes.end() ? 0 : it->second;
     if (it != ctx->sizes.end()) ctx->sizes.erase(it);

@@ -10,6 +10,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <unordered_map>
 #include <utility>
@@ -55,6 +56,7 @@ struct mh_ctx {
     cudaMemPool_t pool = nullptr;
     uint64_t budget = 0, in_use = 0, peak = 0;
     std::unordered_map<void*, size_t> sizes;
+    std::mutex alloc_mu;  // the handles' frees may come from other threads
     int with_mult = 0;
     int num_sms = 0;
     uint32_t* d_status = nullptr;  // device status word (ST_* bits)
