@@ -269,6 +269,10 @@ void* mh_stream(const mh_ctx* ctx);
 
 /* Bytes the context holds now, and the most it has held. */
 void mh_memory(const mh_ctx* ctx, uint64_t* in_use, uint64_t* peak);
+/* Return the device memory the context's own pool keeps cached to the
+ * driver (after finishing the context's stream); no-op with allocator
+ * callbacks.  Errors: MH_EINVAL, MH_EDEVICE. */
+int mh_trim(mh_ctx* ctx);
 
 /* Per-kernel launch statistics gathered while cfg.profile = 1 (or after
  * mh_set_profile(ctx, 1)).  Waits for the stream.  For index i in

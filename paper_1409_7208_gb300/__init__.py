@@ -35,7 +35,7 @@ SYMBOLS = (
     "mh_sdbg_view_get", "mh_free_sdbg", "mh_strerror", "mh_last_error_message", "mh_stream",
     "mh_memory", "mh_profile_count", "mh_profile_get", "mh_profile_reset", "mh_set_profile",
     "mh_sort_keys_noalloc", "mh_walk_contigs", "mh_contigs_view_get", "mh_free_contigs",
-    "mh_pack_reads_contigs",
+    "mh_pack_reads_contigs", "mh_trim",
 )
 
 
@@ -121,6 +121,7 @@ def load_library(path: str = LIB_PATH):
     lib.mh_contigs_view_get.argtypes = [P, ctypes.POINTER(ContigsView)]
     lib.mh_free_contigs.argtypes = [P]
     lib.mh_pack_reads_contigs.argtypes = [P, P, u64, P, u64, P, ctypes.c_int, PP]
+    lib.mh_trim.argtypes = [P]
     _lib = lib
     return lib
 
@@ -215,6 +216,10 @@ class Context:
         if ptr == self.torch_stream.cuda_stream:
             return self.torch_stream
         return torch.cuda.ExternalStream(ptr, device=self.device)
+
+    def trim(self):
+        """Give the memory the library's own pool keeps cached back to the driver."""
+        self._check(self._lib.mh_trim(self._h))
 
     def memory(self):
         a, b = ctypes.c_uint64(), ctypes.c_uint64()

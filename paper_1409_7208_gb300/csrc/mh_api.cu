@@ -461,6 +461,16 @@ const char* mh_last_error_message(const mh_ctx* ctx) { return ctx ? ctx->last_er
 
 void* mh_stream(const mh_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
 
+int mh_trim(mh_ctx* ctx) {
+    if (!ctx) return MH_EINVAL;
+    return guarded(ctx, [&] {
+        if (ctx->pool) {
+            MH_CUDA(cudaStreamSynchronize(ctx->stream));
+            MH_CUDA(cudaMemPoolTrimTo(ctx->pool, 0));
+        }
+    });
+}
+
 void mh_memory(const mh_ctx* ctx, uint64_t* in_use, uint64_t* peak) {
     if (in_use) *in_use = ctx ? ctx->in_use : 0;
     if (peak) *peak = ctx ? ctx->peak : 0;

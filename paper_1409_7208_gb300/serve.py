@@ -137,14 +137,18 @@ class Server:
 
 
 class GpuRunner:
-    """One library context and one CUDA stream per slot."""
+    """One library context and one CUDA stream per slot.  The contexts use
+    the library's own stream-ordered pools (no Python in the allocation
+    path, so the slots' host threads do not contend for the interpreter);
+    a slot trims its pool after a job above ``trim_bytes``."""
 
-    def __init__(self, device: int, slots: int):
+    def __init__(self, device: int, slots: int, trim_bytes: int = 8 << 30):
         import torch
 
         from . import Context
+        self.trim_bytes = trim_bytes
         self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
-        self.ctxs = [Context(device=device, stream=s) for s in self.streams]
+        self.ctxs = [Context(device=device, stream=s, torch_allocator=False) for s in self.streams]
 
     def __call__(self, job: Job, slot: int) -> dict:
         import torch
@@ -158,6 +162,8 @@ class GpuRunner:
             sdbg = mh_build_sdbg(ctx, solid, mercy)
             reads.free()
         s.synchronize()
+        if job.est > self.trim_bytes:
+            ctx.trim()
         return {"solid": solid, "mercy": mercy, "sdbg": sdbg}
 
     def close(self):
