@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256) extract_canonical_kernel(const uint32_t* 
             Key<NW> x = load_window<NW>(packed, b + i, K1);
             Key<NW> r = key_rc<NW>(x, K1);
             Key<NW> c = key_less<NW>(r, x) ? r : x;
-            if constexpr (MIXED) c.w[0] = mix_bij(c.w[0]);
+            if constexpr (MIXED) c = mix_key<NW>(c);
             store_key<NW>(out, w0 + i, c);
         }
     }
@@ -108,7 +108,7 @@ __global__ void run_next_head_kernel(const uint64_t* __restrict__ first, uint64_
 template <int NW>
 __device__ __forceinline__ uint64_t spectrum_count(const uint64_t* __restrict__ spec, uint64_t n_spec, Key<NW> x,
                                                    bool spec_mixed, uint64_t& hint) {
-    if (spec_mixed) x.w[0] = mix_bij(x.w[0]);
+    if (spec_mixed) x = mix_key<NW>(x);
     const uint64_t lb = gallop_lb<NW>(spec, n_spec, x, hint);
     if (lb >= n_spec || !key_eq<NW>(load_key<NW>(spec, lb), x)) {
         hint = lb;
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
         Key<NW> x;
 #pragma unroll
         for (int w = 0; w < NW; w++) x.w[w] = tk[rp(i) * NW + w];
-        if constexpr (IN_MIXED) x.w[0] = unmix_bij(x.w[0]);
+        if constexpr (IN_MIXED) x = unmix_key<NW>(x);
         const bool palin = key_eq<NW>(key_rc<NW>(x, K1), x);
         const uint64_t len = spec ? spectrum_count<NW>(spec, n_spec, x, spec_mixed, hint) : end - (start + i);
         uint64_t c = palin ? 2 * len : len;
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
         Key<NW> xk;
 #pragma unroll
         for (int w = 0; w < NW; w++) xk.w[w] = tk[rp(i) * NW + w];
-        if constexpr (IN_MIXED) xk.w[0] = unmix_bij(xk.w[0]);
+        if constexpr (IN_MIXED) xk = unmix_key<NW>(xk);
         for (uint32_t o = 0; o < nout[j]; o++) {
             const Key<NW> y = o == 0 ? xk : key_rc<NW>(xk, K1);
             if (staged) {
@@ -412,7 +412,6 @@ template <int NW>
 void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, Buf<uint64_t>& out_keys,
                  Buf<uint32_t>& out_cnt, uint64_t* n_out, uint64_t* n_canon_runs, uint64_t* n_palin_runs,
                  const uint64_t* spectrum, uint64_t n_spectrum, bool in_mixed, bool spec_mixed, KeptList* kept) {
-    if (NW != 1 && (in_mixed || spec_mixed)) fail(MH_EUNSUPPORTED, "mixed keys are 1-word keys");
     if (kept && (NW != 1 || spectrum)) fail(MH_EUNSUPPORTED, "kept-run lists are for 1-word counting");
     const int K1 = k + 1;
     const uint64_t tiles = ceil_div(n ? n : 1, kRunTile);
@@ -498,16 +497,15 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
     uint64_t n;
     read_u64(ctx, woff.p + F, &n, 1);
     nwin.reset();
-    // 1-word keys are sorted through mix_bij: spread top bits let the sort
-    // run its passes over the top ceil(log2 n) + 8 bits only
-    constexpr bool kMixed = NW == 1;
+    // keys are sorted as mix_key images: their evenly spread top bits let
+    // the sort run its passes over the top ceil(log2 n) bits only
+    constexpr bool kMixed = true;
     Buf<uint64_t> keys(ctx, (n ? n : 1) * NW), alt(ctx, (n ? n : 1) * NW);
     if (n)
         MH_LAUNCH_B(ctx, "extract_canonical", reads->n_packed / 4 + n * 8 * NW, grid_for(ctx, F * 32, 256, 8), 256, 0,
                     (extract_canonical_kernel<NW, kMixed>), reads->packed, reads->frag_offs, woff.p, F, k, keys.p);
     woff.reset();
-    bool in_alt = kMixed ? radix_sort_spread(ctx, keys.p, alt.p, n)
-                         : radix_sort<NW>(ctx, keys.p, alt.p, nullptr, nullptr, n, 0, 2 * (k + 1));
+    bool in_alt = radix_sort_spread<NW>(ctx, keys.p, alt.p, n);
     Buf<uint64_t>& spec = in_alt ? alt : keys;
     Buf<uint64_t>& other = in_alt ? keys : alt;
     Buf<uint64_t> sk;
@@ -516,10 +514,11 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
     // 1-word keys: the kept canonical keys (mixed, ascending) are listed too,
     // in the free sort buffer
     KeptList kept;
-    if (kMixed) kept.slot = std::move(other);
+    constexpr bool kList = kMixed && NW == 1;
+    if (kList) kept.slot = std::move(other);
     other.reset();
     expand_runs<NW>(ctx, spec.p, n, k, d, sk, sc, &S, &runs, &palins, nullptr, 0, kMixed, false,
-                    kMixed ? &kept : nullptr);
+                    kList ? &kept : nullptr);
     sync_and_check(ctx);
     out->k = k;
     out->nw = NW;
@@ -532,7 +531,7 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
     out->n_spectrum = n;
     out->spectrum_mixed = kMixed;
     out->spectrum = spec.release();
-    if (kMixed) {
+    if (kList) {
         out->n_canon = kept.n;
         out->canon = kept.keys.release();
     }

@@ -545,6 +545,26 @@ __host__ __device__ __forceinline__ uint64_t unmix_bij(uint64_t h) {
     return h * kMixC1Inv;
 }
 
+// Multiword keys: word i is mixed together with the mixed word below it, so
+// the top word depends on every word (its top bits spread evenly) and each
+// step can be undone given the word below (a bijection of keys).  One word:
+// mix_bij.
+template <int NW>
+__host__ __device__ __forceinline__ Key<NW> mix_key(Key<NW> a) {
+    a.w[0] = mix_bij(a.w[0]);
+#pragma unroll
+    for (int i = 1; i < NW; i++) a.w[i] = mix_bij(a.w[i] ^ a.w[i - 1]);
+    return a;
+}
+template <int NW>
+__host__ __device__ __forceinline__ Key<NW> unmix_key(const Key<NW>& m) {
+    Key<NW> a;
+#pragma unroll
+    for (int i = NW - 1; i >= 1; i--) a.w[i] = unmix_bij(m.w[i]) ^ m.w[i - 1];
+    a.w[0] = unmix_bij(m.w[0]);
+    return a;
+}
+
 template <int NW>
 __device__ __forceinline__ uint64_t key_hash(const Key<NW>& a) {
     uint64_t h = 0x9E3779B97F4A7C15ull;
@@ -566,6 +586,7 @@ bool radix_sort(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint
 // k-mers): LSD passes over the top P = ceil(log2 n) + 8 bits only (whole
 // digits), then the rare groups of distinct keys sharing those bits are put
 // in order.  Returns true if the result is in alt.
+template <int NW>
 bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n);
 
 // ---------------------------------------------------------------- scans

@@ -358,8 +358,9 @@ __global__ void __launch_bounds__(256) mercy_probe_kernel(const uint32_t* __rest
 }
 
 // Walk from each hit to the next solid window; emit the gap if it qualifies.
-// MIXED (1-word keys): solidity from the ascending mixed solid keys `canon`
-// with its bucket index; otherwise from the hash set `solid`.
+// MIXED: candidates out as mix_key images; 1-word keys then take solidity
+// from the ascending mixed solid keys `canon` with its bucket index, wider
+// keys (and unmixed handles) from the hash set `solid`.
 template <int NW, bool MIXED>
 __global__ void __launch_bounds__(256) mercy_walk_kernel(const uint32_t* __restrict__ packed,
                                                          const ulonglong2* __restrict__ hits, uint64_t n_hits, int k,
@@ -381,7 +382,7 @@ __global__ void __launch_bounds__(256) mercy_walk_kernel(const uint32_t* __restr
             Key<NW> r = key_rc<NW>(x, K1);
             const Key<NW> c = key_less<NW>(r, x) ? r : x;
             bool present;
-            if constexpr (MIXED)
+            if constexpr (MIXED && NW == 1)
                 present = canon_has(canon, canon_off, canon_bits, mix_bij(c.w[0]));
             else
                 present = table_has<NW>(solid, solid_mask, c);
@@ -398,7 +399,7 @@ __global__ void __launch_bounds__(256) mercy_walk_kernel(const uint32_t* __restr
             Key<NW> z = load_window<NW>(packed, j, K1);
             Key<NW> rz = key_rc<NW>(z, K1);
             Key<NW> c = key_less<NW>(rz, z) ? rz : z;
-            if constexpr (MIXED) c.w[0] = mix_bij(c.w[0]);
+            if constexpr (MIXED) c = mix_key<NW>(c);
             store_key<NW>(out, idx, c);
         }
     }
@@ -444,13 +445,13 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
     // solidity: 1-word keys use the counting handle's ascending mixed solid
     // keys with a bucket index (4 to 8 keys a bucket); wider keys a hash set
     // of the canonical solid keys, load <= 1/2 (<= 0.61 if all palindromes)
-    const bool mixed = NW == 1 && solid->spectrum_mixed;
-    if (mixed && !solid->canon && S) fail(MH_EINVAL, "the solid handle must come from mh_count_kmers");
+    const bool mixed = solid->spectrum_mixed;
+    if (NW == 1 && mixed && !solid->canon && S) fail(MH_EINVAL, "the solid handle must come from mh_count_kmers");
     Buf<Slot<NW>> sset;
     uint64_t scap = 1;
     Buf<uint64_t> canon_off;
     int canon_bits = 1;
-    if (mixed) {
+    if (NW == 1 && mixed) {
         while (canon_bits < 40 && (2ull << canon_bits) * 4 <= solid->n_canon) canon_bits++;
         canon_off = Buf<uint64_t>(ctx, (1ull << canon_bits) + 1);
         canon_off.zero();
@@ -481,7 +482,7 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
         hit_cap = n_hits;
     }
     // the gaps behind the hits
-    // candidates in the spectrum's order (mixed 1-word keys), so that their
+    // candidates in the spectrum's order (mix_key images), so that their
     // sorted spectrum lookups ascend
     uint64_t out_cap = std::max<uint64_t>(1u << 20, 16 * n_hits);
     Buf<uint64_t> cand;
@@ -503,7 +504,8 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
     canon_off.reset();
     table.reset();
     Buf<uint64_t> alt(ctx, (n_cand ? n_cand : 1) * NW);
-    bool in_alt = radix_sort<NW>(ctx, cand.p, alt.p, nullptr, nullptr, n_cand, 0, mixed ? 64 : 2 * (k + 1));
+    bool in_alt = mixed ? radix_sort_spread<NW>(ctx, cand.p, alt.p, n_cand)
+                        : radix_sort<NW>(ctx, cand.p, alt.p, nullptr, nullptr, n_cand, 0, 2 * (k + 1));
     Buf<uint64_t>& sorted = in_alt ? alt : cand;
     Buf<uint64_t> mk;
     Buf<uint32_t> mc;

@@ -114,31 +114,33 @@ template bool radix_sort<2>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*,
 template bool radix_sort<4>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*, uint64_t, int, int);
 
 // ------------------------------------------------------------ spread sort
-// The keys are mix_bij images, so their top bits are evenly spread: LSD
-// passes over the top P bits only (P = ceil(log2 n) rounded up to a digit)
-// leave every group of equal top bits in input order, and a group holds
-// more than one distinct key only where two keys collide on those P bits
-// (about D^2 / 2^(P+1) groups for D distinct keys).  The fix-up sorts such
-// groups.  A tile kernel reads 2048 keys (plus 256 past the tile, for the
-// group that crosses its end), finds the groups that start in the tile and
-// contain a descent, and sorts them: up to 16 keys by one thread (insertion
-// sort), larger ones by one warp (successive minima: each round finds the
-// smallest key above the previous one and its count, then writes that run).
-// Groups that do not end inside the window, or have more than 64 distinct
-// keys, go to a list for a CTA each (successive minima over the group in
-// global memory, written through the free buffer); more than 256 distinct
-// keys there (pathological) fall back to a radix sort of the segment.
+// The keys are mix_key images, so the top bits of their top word are evenly
+// spread: LSD passes over the top P bits only (P = ceil(log2 n) rounded up
+// to a digit) leave every group of equal top bits in input order, and a
+// group holds more than one distinct key only where two keys collide on
+// those P bits (about D^2 / 2^(P+1) groups for D distinct keys).  The fix-up
+// sorts such groups.  A tile kernel reads a window of keys (2048 / nw plus
+// 256 / nw past the tile, for the group that crosses its end), finds the
+// groups that start in the tile and contain a descent, and sorts them: up to
+// 16 keys by one thread (insertion sort), larger ones by one warp
+// (successive minima: each round finds the smallest key above the previous
+// one and its count, then writes that run).  Groups that do not end inside
+// the window, or have more than 64 distinct keys, go to a list for a CTA
+// each (successive minima over the group in global memory, written through
+// the free buffer); more than 256 distinct keys there (pathological) fall
+// back to a radix sort of the segment.
 
-constexpr int kFixTile = 2048;
-constexpr int kFixExt = 256;
-constexpr int kFixWin = kFixTile + kFixExt;
-constexpr int kFixWords = kFixWin / 32;
-constexpr int kFixThreadSort = 16;
-constexpr int kFixQueue = kFixWin / (kFixThreadSort + 1) + 1;  // groups of > 16 keys in a window
+template <int NW>
+struct Fix {
+    static constexpr int kTile = 2048 / NW;
+    static constexpr int kExt = 256 / NW;
+    static constexpr int kWin = kTile + kExt;
+    static constexpr int kWords = kWin / 32;
+    static constexpr int kThreadSort = 16;
+    static constexpr int kQueue = kWin / (kThreadSort + 1) + 1;  // groups of > 16 keys in a window
+};
 constexpr int kFixWarpRounds = 64;
 constexpr int kFixBlockRounds = 256;
-
-__device__ __forceinline__ bool bit_of(const uint32_t* b, uint32_t i) { return (b[i >> 5] >> (i & 31)) & 1u; }
 
 // First set bit at or after i in b (bits [0, n)), or n.
 __device__ __forceinline__ uint32_t next_bit(const uint32_t* b, uint32_t i, uint32_t n) {
@@ -160,40 +162,68 @@ __device__ __forceinline__ bool any_bit(const uint32_t* b, uint32_t i, uint32_t 
     return next_bit(b, i, j) < j;
 }
 
+template <int NW>
+__device__ __forceinline__ Key<NW> shfl_key(const Key<NW>& a, int src_lane_xor) {
+    Key<NW> r;
+#pragma unroll
+    for (int w = 0; w < NW; w++) r.w[w] = __shfl_xor_sync(0xFFFFFFFFu, a.w[w], src_lane_xor);
+    return r;
+}
+
+template <int NW>
+__device__ __forceinline__ Key<NW> key_ones() {
+    Key<NW> r;
+#pragma unroll
+    for (int w = 0; w < NW; w++) r.w[w] = ~0ull;
+    return r;
+}
+
+template <int NW>
 __global__ void __launch_bounds__(256) spread_fix_kernel(uint64_t* __restrict__ keys, uint64_t n, int lo,
                                                          uint64_t* __restrict__ big, uint64_t big_cap,
                                                          unsigned long long* __restrict__ n_big) {
-    __shared__ uint64_t K[kFixWin];
-    __shared__ uint32_t head[kFixWords], desc[kFixWords];
-    __shared__ uint32_t queue[2 * kFixQueue];  // (start, end) of the groups for warps
+    using F = Fix<NW>;
+    __shared__ uint64_t K[F::kWin * NW];
+    __shared__ uint32_t head[F::kWords], desc[F::kWords];
+    __shared__ uint32_t queue[2 * F::kQueue];  // (start, end) of the groups for warps
     __shared__ uint32_t n_queue;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint64_t s = blockIdx.x * (uint64_t)kFixTile;
-    const uint32_t W = (uint32_t)(n - s < (uint64_t)kFixWin ? n - s : (uint64_t)kFixWin);
-    const uint32_t len = W < (uint32_t)kFixTile ? W : (uint32_t)kFixTile;
+    const uint64_t s = blockIdx.x * (uint64_t)F::kTile;
+    const uint32_t W = (uint32_t)(n - s < (uint64_t)F::kWin ? n - s : (uint64_t)F::kWin);
+    const uint32_t len = W < (uint32_t)F::kTile ? W : (uint32_t)F::kTile;
     const bool window_ends_array = s + W == n;
-    if (W == (uint32_t)kFixWin) {
+    auto kget = [&](uint32_t i) {
+        Key<NW> r;
+#pragma unroll
+        for (int w = 0; w < NW; w++) r.w[w] = K[i * NW + w];
+        return r;
+    };
+    auto kset = [&](uint32_t i, const Key<NW>& x) {
+#pragma unroll
+        for (int w = 0; w < NW; w++) K[i * NW + w] = x.w[w];
+    };
+    if (W == (uint32_t)F::kWin) {
         // all loads in flight at once
-        uint64_t v[kFixWin / 256];
+        uint64_t v[F::kWin * NW / 256];
 #pragma unroll
-        for (int q = 0; q < kFixWin / 256; q++) v[q] = keys[s + tid + q * 256];
+        for (int q = 0; q < F::kWin * NW / 256; q++) v[q] = keys[s * NW + tid + q * 256];
 #pragma unroll
-        for (int q = 0; q < kFixWin / 256; q++) K[tid + q * 256] = v[q];
+        for (int q = 0; q < F::kWin * NW / 256; q++) K[tid + q * 256] = v[q];
     } else {
-        for (uint32_t i = tid; i < W; i += 256) K[i] = keys[s + i];
+        for (uint32_t i = tid; i < W * NW; i += 256) K[i] = keys[s * NW + i];
     }
     if (tid == 0) n_queue = 0;
     __syncthreads();
-    // a and b share their top bits iff (a ^ b) < 2^lo
+    // a and b share their top bits iff (a ^ b) < 2^lo in the top word
     const uint64_t same_top = 1ull << lo;
-    for (uint32_t wd = warp; wd < (uint32_t)kFixWords; wd += 8) {
+    for (uint32_t wd = warp; wd < (uint32_t)F::kWords; wd += 8) {
         const uint32_t i = wd * 32 + lane;
         bool h = false, d = false;
         if (i < W) {
-            const uint64_t x = K[i];
-            const uint64_t y = i > 0 ? K[i - 1] : (s > 0 ? keys[s - 1] : ~x);
-            h = (x ^ y) >= same_top;
-            d = i > 0 && !h && x < y;
+            const Key<NW> x = kget(i);
+            const Key<NW> y = i > 0 ? kget(i - 1) : (s > 0 ? load_key<NW>(keys, s - 1) : key_ones<NW>());
+            h = i == 0 && s == 0 ? true : (x.w[NW - 1] ^ y.w[NW - 1]) >= same_top;
+            d = i > 0 && !h && key_less<NW>(x, y);
         }
         const uint32_t hb = __ballot_sync(0xFFFFFFFFu, h), db = __ballot_sync(0xFFFFFFFFu, d);
         if (lane == 0) {
@@ -202,11 +232,12 @@ __global__ void __launch_bounds__(256) spread_fix_kernel(uint64_t* __restrict__ 
         }
     }
     __syncthreads();
-    // groups starting in this tile: thread per 8 positions, visiting their heads
-    uint32_t hm = tid * 8 < len ? (head[tid >> 2] >> ((tid & 3) * 8)) & 0xFFu : 0u;
-    if (tid * 8 + 8 > len) hm &= (1u << (len - tid * 8)) - 1u;
+    // groups starting in this tile: thread per 8 / NW positions, visiting their heads
+    constexpr int PER = 8 / NW;
+    uint32_t hm = tid * PER < len ? (head[(tid * PER) >> 5] >> ((tid * PER) & 31)) & ((1u << PER) - 1u) : 0u;
+    if (tid * PER + PER > len) hm &= (1u << (len > tid * PER ? len - tid * PER : 0)) - 1u;
     while (hm) {
-        const uint32_t h = tid * 8 + __ffs(hm) - 1;
+        const uint32_t h = tid * PER + __ffs(hm) - 1;
         hm &= hm - 1;
         const uint32_t g1 = next_bit(head, h + 1, W);
         if (g1 == W && !window_ends_array) {
@@ -216,17 +247,17 @@ __global__ void __launch_bounds__(256) spread_fix_kernel(uint64_t* __restrict__ 
             continue;
         }
         if (!any_bit(desc, h + 1, g1)) continue;
-        if (g1 - h <= (uint32_t)kFixThreadSort) {
+        if (g1 - h <= (uint32_t)F::kThreadSort) {
             for (uint32_t j = h + 1; j < g1; j++) {
-                const uint64_t x = K[j];
+                const Key<NW> x = kget(j);
                 uint32_t i = j;
-                while (i > h && K[i - 1] > x) {
-                    K[i] = K[i - 1];
+                while (i > h && key_less<NW>(x, kget(i - 1))) {
+                    kset(i, kget(i - 1));
                     i--;
                 }
-                K[i] = x;
+                kset(i, x);
             }
-            for (uint32_t j = h; j < g1; j++) keys[s + j] = K[j];
+            for (uint32_t j = h; j < g1; j++) store_key<NW>(keys, s + j, kget(j));
         } else {
             const uint32_t q = atomicAdd(&n_queue, 1u);
             queue[2 * q] = h;
@@ -239,24 +270,32 @@ __global__ void __launch_bounds__(256) spread_fix_kernel(uint64_t* __restrict__ 
     for (uint32_t q = warp; q < nq; q += 8) {
         const uint32_t g0 = queue[2 * q], g1 = queue[2 * q + 1];
         uint32_t pos = g0;
-        uint64_t prev = 0;
+        Key<NW> prev = key_zero<NW>();
         bool first = true;
         int rounds = 0;
         while (pos < g1 && rounds < kFixWarpRounds) {
             // smallest key above prev, and its count
-            uint64_t mn = ~0ull;
+            Key<NW> mn = key_ones<NW>();
+            bool have = false;
             for (uint32_t i = g0 + lane; i < g1; i += 32) {
-                const uint64_t x = K[i];
-                if ((first || x > prev) && x < mn) mn = x;
+                const Key<NW> x = kget(i);
+                if ((first || key_less<NW>(prev, x)) && (!have || key_less<NW>(x, mn))) {
+                    mn = x;
+                    have = true;
+                }
             }
             for (int off = 16; off; off >>= 1) {
-                const uint64_t o = __shfl_xor_sync(0xFFFFFFFFu, mn, off);
-                mn = o < mn ? o : mn;
+                const Key<NW> o = shfl_key<NW>(mn, off);
+                const bool oh = __shfl_xor_sync(0xFFFFFFFFu, have, off);
+                if (oh && (!have || key_less<NW>(o, mn))) {
+                    mn = o;
+                    have = true;
+                }
             }
             uint32_t c = 0;
-            for (uint32_t i = g0 + lane; i < g1; i += 32) c += K[i] == mn;
+            for (uint32_t i = g0 + lane; i < g1; i += 32) c += key_eq<NW>(kget(i), mn);
             for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, off);
-            for (uint32_t i = lane; i < c; i += 32) keys[s + pos + i] = mn;
+            for (uint32_t i = lane; i < c; i += 32) store_key<NW>(keys, s + pos + i, mn);
             pos += c;
             prev = mn;
             first = false;
@@ -264,7 +303,7 @@ __global__ void __launch_bounds__(256) spread_fix_kernel(uint64_t* __restrict__ 
         }
         if (pos < g1 && lane == 0) {
             // too many distinct keys: rewrite the group as it was and defer it
-            for (uint32_t i = g0; i < g1; i++) keys[s + i] = K[i];
+            for (uint32_t i = g0; i < g1; i++) store_key<NW>(keys, s + i, kget(i));
             const unsigned long long b = atomicAdd(n_big, 1ull);
             if (b < big_cap) big[b] = s + g0;
         }
@@ -273,18 +312,21 @@ __global__ void __launch_bounds__(256) spread_fix_kernel(uint64_t* __restrict__ 
 
 // A CTA per listed group start: find the group's end, skip it if sorted,
 // else sort it by successive minima through tmp (the free buffer).
+template <int NW>
 __global__ void __launch_bounds__(256) spread_big_kernel(uint64_t* __restrict__ keys, uint64_t* __restrict__ tmp,
                                                          uint64_t n, int lo, const uint64_t* __restrict__ list,
                                                          uint64_t n_list, ulonglong2* __restrict__ rest,
                                                          unsigned long long* __restrict__ n_rest) {
     __shared__ uint64_t s_end;
-    __shared__ uint64_t red64[8];
+    __shared__ uint64_t redk[8 * NW];
+    __shared__ uint32_t redh[8];
     __shared__ uint32_t red32[8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    auto top = [&](uint64_t i) { return keys[i * NW + NW - 1] >> lo; };
     for (uint64_t g = blockIdx.x; g < n_list; g += gridDim.x) {
         const uint64_t gs = list[g];
         if (tid == 0) {
-            const uint64_t px = keys[gs] >> lo;
+            const uint64_t px = top(gs);
             uint64_t l = gs + 1, step = 1, h;
             while (true) {  // first index with other top bits
                 const uint64_t probe = l + step - 1;
@@ -292,7 +334,7 @@ __global__ void __launch_bounds__(256) spread_big_kernel(uint64_t* __restrict__ 
                     h = n;
                     break;
                 }
-                if ((keys[probe] >> lo) != px) {
+                if (top(probe) != px) {
                     h = probe;
                     break;
                 }
@@ -301,7 +343,7 @@ __global__ void __launch_bounds__(256) spread_big_kernel(uint64_t* __restrict__ 
             }
             while (l < h) {
                 const uint64_t mid = (l + h) / 2;
-                if ((keys[mid] >> lo) == px) l = mid + 1; else h = mid;
+                if (top(mid) == px) l = mid + 1; else h = mid;
             }
             s_end = l;
         }
@@ -309,35 +351,57 @@ __global__ void __launch_bounds__(256) spread_big_kernel(uint64_t* __restrict__ 
         const uint64_t ge = s_end;
         // sorted already?
         uint32_t d = 0;
-        for (uint64_t i = gs + 1 + tid; i < ge; i += 256) d |= keys[i] < keys[i - 1];
+        for (uint64_t i = gs + 1 + tid; i < ge; i += 256)
+            d |= key_less<NW>(load_key<NW>(keys, i), load_key<NW>(keys, i - 1));
         d = __syncthreads_or(d);
         if (!d) continue;
-        uint64_t pos = gs, prev = 0;
+        uint64_t pos = gs;
+        Key<NW> prev = key_zero<NW>();
         bool first = true;
         int rounds = 0;
         while (pos < ge && rounds < kFixBlockRounds) {
-            uint64_t mn = ~0ull;
-            uint32_t c = 0;
+            Key<NW> mn = key_ones<NW>();
+            bool have = false;
             for (uint64_t i = gs + tid; i < ge; i += 256) {
-                const uint64_t x = keys[i];
-                if ((first || x > prev) && x < mn) mn = x;
+                const Key<NW> x = load_key<NW>(keys, i);
+                if ((first || key_less<NW>(prev, x)) && (!have || key_less<NW>(x, mn))) {
+                    mn = x;
+                    have = true;
+                }
             }
             for (int off = 16; off; off >>= 1) {
-                const uint64_t o = __shfl_xor_sync(0xFFFFFFFFu, mn, off);
-                mn = o < mn ? o : mn;
+                const Key<NW> o = shfl_key<NW>(mn, off);
+                const bool oh = __shfl_xor_sync(0xFFFFFFFFu, have, off);
+                if (oh && (!have || key_less<NW>(o, mn))) {
+                    mn = o;
+                    have = true;
+                }
             }
-            if (lane == 0) red64[warp] = mn;
+            if (lane == 0) {
+#pragma unroll
+                for (int w = 0; w < NW; w++) redk[warp * NW + w] = mn.w[w];
+                redh[warp] = have;
+            }
             __syncthreads();
-            mn = red64[0];
-            for (int w = 1; w < 8; w++) mn = red64[w] < mn ? red64[w] : mn;
-            for (uint64_t i = gs + tid; i < ge; i += 256) c += keys[i] == mn;
+            have = false;
+            for (int wv = 0; wv < 8; wv++) {
+                Key<NW> o;
+#pragma unroll
+                for (int w = 0; w < NW; w++) o.w[w] = redk[wv * NW + w];
+                if (redh[wv] && (!have || key_less<NW>(o, mn))) {
+                    mn = o;
+                    have = true;
+                }
+            }
+            uint32_t c = 0;
+            for (uint64_t i = gs + tid; i < ge; i += 256) c += key_eq<NW>(load_key<NW>(keys, i), mn);
             for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, off);
             __syncthreads();
             if (lane == 0) red32[warp] = c;
             __syncthreads();
             c = 0;
             for (int w = 0; w < 8; w++) c += red32[w];
-            for (uint64_t i = tid; i < c; i += 256) tmp[pos + i] = mn;
+            for (uint64_t i = tid; i < c; i += 256) store_key<NW>(tmp, pos + i, mn);
             pos += c;
             prev = mn;
             first = false;
@@ -347,7 +411,7 @@ __global__ void __launch_bounds__(256) spread_big_kernel(uint64_t* __restrict__ 
         if (pos < ge) {
             if (tid == 0) rest[atomicAdd(n_rest, 1ull)] = make_ulonglong2(gs, ge);
         } else {
-            for (uint64_t i = gs + tid; i < ge; i += 256) keys[i] = tmp[i];
+            for (uint64_t i = gs * NW + tid; i < ge * NW; i += 256) keys[i] = tmp[i];
         }
         __syncthreads();
     }
@@ -370,28 +434,31 @@ static int spread_bits(uint64_t n) {
     return forced ? forced : std::max(8, ((ceil_log2(n) + 7) / 8) * 8);
 }
 
+template <int NW>
 bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n) {
+    using F = Fix<NW>;
     const int P = spread_bits(n);
-    if (n <= 1 || P >= 64) return radix_sort<1>(ctx, keys, alt, nullptr, nullptr, n, 0, 64);
-    const int lo = 64 - P;
-    const bool in_alt = radix_sort<1>(ctx, keys, alt, nullptr, nullptr, n, lo, 64);
+    const int bits = 64 * NW;
+    if (n <= 1 || P >= 64) return radix_sort<NW>(ctx, keys, alt, nullptr, nullptr, n, 0, bits);
+    const int lo = 64 - P;  // within the top word
+    const bool in_alt = radix_sort<NW>(ctx, keys, alt, nullptr, nullptr, n, bits - P, bits);
     uint64_t* k = in_alt ? alt : keys;
     uint64_t* other = in_alt ? keys : alt;
     const uint64_t cap = std::max<uint64_t>(1 << 16, n / 64);
     Buf<uint64_t> list(ctx, cap), cnt(ctx, 2);
     cnt.zero();
-    MH_LAUNCH_B(ctx, "spread_fixup", n * 8, (unsigned)ceil_div(n, kFixTile), 256, 0, spread_fix_kernel, k, n, lo,
-                list.p, cap, (unsigned long long*)cnt.p);
+    MH_LAUNCH_B(ctx, "spread_fixup", n * 8 * NW, (unsigned)ceil_div(n, F::kTile), 256, 0, spread_fix_kernel<NW>, k,
+                n, lo, list.p, cap, (unsigned long long*)cnt.p);
     uint64_t n_big = 0;
     read_u64(ctx, cnt.p, &n_big, 1);
     if (n_big > cap) {
         // far more long or crowded groups than evenly spread keys give: sort fully
-        return in_alt != radix_sort<1>(ctx, k, other, nullptr, nullptr, n, 0, 64);
+        return in_alt != radix_sort<NW>(ctx, k, other, nullptr, nullptr, n, 0, bits);
     }
     if (n_big) {
         Buf<ulonglong2> rest(ctx, n_big);
         MH_LAUNCH(ctx, "spread_fixup_big", (unsigned)std::min<uint64_t>(n_big, (uint64_t)ctx->num_sms * 8), 256, 0,
-                  spread_big_kernel, k, other, n, lo, list.p, n_big, rest.p, (unsigned long long*)(cnt.p + 1));
+                  spread_big_kernel<NW>, k, other, n, lo, list.p, n_big, rest.p, (unsigned long long*)(cnt.p + 1));
         uint64_t n_rest = 0;
         read_u64(ctx, cnt.p + 1, &n_rest, 1);
         if (n_rest) {
@@ -401,13 +468,18 @@ bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n) {
             sync_and_check(ctx);
             for (const ulonglong2& seg : h) {
                 const uint64_t len = seg.y - seg.x;
-                if (radix_sort<1>(ctx, k + seg.x, other + seg.x, nullptr, nullptr, len, 0, lo))
-                    MH_CUDA(cudaMemcpyAsync(k + seg.x, other + seg.x, len * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+                if (radix_sort<NW>(ctx, k + seg.x * NW, other + seg.x * NW, nullptr, nullptr, len, 0, bits - P))
+                    MH_CUDA(cudaMemcpyAsync(k + seg.x * NW, other + seg.x * NW, len * 8 * NW, cudaMemcpyDeviceToDevice,
+                                            ctx->stream));
             }
         }
     }
     return in_alt;
 }
+
+template bool radix_sort_spread<1>(mh_ctx*, uint64_t*, uint64_t*, uint64_t);
+template bool radix_sort_spread<2>(mh_ctx*, uint64_t*, uint64_t*, uint64_t);
+template bool radix_sort_spread<4>(mh_ctx*, uint64_t*, uint64_t*, uint64_t);
 
 // ------------------------------------------------------------------ scans
 constexpr int kScanThreads = 256;
