@@ -356,7 +356,7 @@ int mh_count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers** 
 int mh_mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_kmers** out) {
     if (!ctx || !reads || !solid || !out) return MH_EINVAL;
     *out = nullptr;
-    if (!solid->spectrum && solid->n_spectrum) {
+    if (!solid->spectrum) {
         ctx->last_error = "mh_mercy_kmers: the solid handle must come from mh_count_kmers";
         return MH_EINVAL;
     }
@@ -390,7 +390,7 @@ void mh_free_kmers(mh_kmers* s) {
     ctx_free(s->ctx, s->keys);
     ctx_free(s->ctx, s->counts);
     ctx_free(s->ctx, s->spectrum);
-    ctx_free(s->ctx, s->canon);
+    ctx_free(s->ctx, s->spectrum_len);
     delete s;
 }
 

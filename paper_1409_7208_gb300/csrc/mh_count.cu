@@ -102,39 +102,19 @@ __global__ void run_next_head_kernel(const uint64_t* __restrict__ first, uint64_
     }
 }
 
-// Number of copies of x in the sorted spectrum (of mix_bij images when
-// spec_mixed), searching outward from `hint` and leaving it after the copies:
-// a thread's queries ascend, so each search starts near the previous answer.
+// Run length of x in the spectrum (distinct canonical keys, ascending, as
+// mix_key images when spec_mixed, with the length of each key's run), or 0;
+// the search starts from `hint`, left at the answer: a thread's queries
+// ascend, so each search starts near the previous one.
 template <int NW>
-__device__ __forceinline__ uint64_t spectrum_count(const uint64_t* __restrict__ spec, uint64_t n_spec, Key<NW> x,
+__device__ __forceinline__ uint64_t spectrum_count(const uint64_t* __restrict__ spec,
+                                                   const uint32_t* __restrict__ spec_len, uint64_t n_spec, Key<NW> x,
                                                    bool spec_mixed, uint64_t& hint) {
     if (spec_mixed) x = mix_key<NW>(x);
     const uint64_t lb = gallop_lb<NW>(spec, n_spec, x, hint);
-    if (lb >= n_spec || !key_eq<NW>(load_key<NW>(spec, lb), x)) {
-        hint = lb;
-        return 0;
-    }
-    // first index after lb holding another key
-    uint64_t lo = lb, step = 1, hi;
-    while (true) {
-        const uint64_t probe = lo + step;
-        if (probe >= n_spec) {
-            hi = n_spec;
-            break;
-        }
-        if (!key_eq<NW>(load_key<NW>(spec, probe), x)) {
-            hi = probe;
-            break;
-        }
-        lo = probe;
-        step <<= 1;
-    }
-    while (hi - lo > 1) {
-        const uint64_t mid = lo + (hi - lo) / 2;
-        if (key_eq<NW>(load_key<NW>(spec, mid), x)) lo = mid; else hi = mid;
-    }
-    hint = hi;
-    return hi - lb;
+    hint = lb;
+    if (lb >= n_spec || !key_eq<NW>(load_key<NW>(spec, lb), x)) return 0;
+    return spec_len[lb];
 }
 
 // Counting mode (spec == nullptr): a run of length len is the canonical key
@@ -148,15 +128,17 @@ __device__ __forceinline__ uint64_t spectrum_count(const uint64_t* __restrict__ 
 // the palindrome test, output) is not repeated for every key of a run.
 template <int NW, bool IN_MIXED>
 __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __restrict__ s, uint64_t n, int K1, int d,
-                                                           const uint64_t* __restrict__ spec, uint64_t n_spec,
+                                                           const uint64_t* __restrict__ spec,
+                                                           const uint32_t* __restrict__ spec_len, uint64_t n_spec,
                                                            bool spec_mixed,
                                                            const uint64_t* __restrict__ next_head,
                                                            uint64_t* __restrict__ out_keys,
                                                            uint32_t* __restrict__ out_cnt, uint32_t slot,
                                                            uint32_t* __restrict__ tile_count,
                                                            uint2* __restrict__ tile_stats,
-                                                           uint64_t* __restrict__ kept_slot,
-                                                           uint32_t* __restrict__ kept_count,
+                                                           uint64_t* __restrict__ run_keys,
+                                                           uint32_t* __restrict__ run_len,
+                                                           uint32_t* __restrict__ run_count,
                                                            uint32_t* __restrict__ err) {
     constexpr int kWords = kRunTile / 32;
     constexpr int kRunsPerThread = kRunTile / kRunThreads;
@@ -167,8 +149,7 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
     uint32_t* head_bits = reinterpret_cast<uint32_t*>(tk + kRunTilePad * NW);  // [TILE / 32]
     uint32_t* wpre = head_bits + kWords;                                       // [TILE / 32 + 1] (+7 pad)
     uint32_t* wsum = wpre + kWords + 8;                                        // [8]
-    uint32_t* wkept = wsum + 8;                                                // [rounds 8][warps 8]
-    uint16_t* hp = reinterpret_cast<uint16_t*>(wkept + 64);                    // [TILE] head positions
+    uint16_t* hp = reinterpret_cast<uint16_t*>(wsum + 8);                      // [TILE] head positions
     uint64_t* out_stage_k = reinterpret_cast<uint64_t*>(hp + kRunTile);        // [TILE] if NW == 1
     uint32_t* out_stage_c = reinterpret_cast<uint32_t*>(out_stage_k + (NW == 1 ? kRunTile : 0));  // [TILE]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -251,7 +232,13 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
         for (int w = 0; w < NW; w++) x.w[w] = tk[rp(i) * NW + w];
         if constexpr (IN_MIXED) x = unmix_key<NW>(x);
         const bool palin = key_eq<NW>(key_rc<NW>(x, K1), x);
-        const uint64_t len = spec ? spectrum_count<NW>(spec, n_spec, x, spec_mixed, hint) : end - (start + i);
+        const uint64_t len = spec ? spectrum_count<NW>(spec, spec_len, n_spec, x, spec_mixed, hint) : end - (start + i);
+        if (run_keys) {
+            // every run, in run order at the tile's own offset (mixed key, length)
+#pragma unroll
+            for (int w = 0; w < NW; w++) run_keys[(start + r) * NW + w] = tk[rp(i) * NW + w];
+            run_len[start + r] = (uint32_t)(len < 0xFFFFFFFFull ? len : 0xFFFFFFFFull);
+        }
         uint64_t c = palin ? 2 * len : len;
         if (c > 0xFFFFFFFFull) {
             atomicOr(err, ST_OVERFLOW);
@@ -262,19 +249,6 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
         outs += nout[j];
         palins += palin;
     }
-    // kept runs per warp and round (for the run-ordered kept list; read after
-    // the block scan's barriers)
-    const bool list_kept = NW == 1 && kept_slot != nullptr;
-    uint32_t kbal[kRunsPerThread];
-    if (list_kept) {
-#pragma unroll
-        for (int j = 0; j < kRunsPerThread; j++) {
-            kbal[j] = 0;
-            if ((uint32_t)(j * kRunThreads) >= H) break;
-            kbal[j] = __ballot_sync(0xFFFFFFFFu, nout[j] != 0);
-            if (lane == 0) wkept[j * 8 + warp] = __popc(kbal[j]);
-        }
-    }
     // one block scan of (outputs | palindromic runs << 16): both fit 16 bits
     uint32_t total;
     const uint32_t excl_thread = block_excl_scan_256(outs | (palins << 16), wsum, &total) & 0xFFFFu;
@@ -282,30 +256,11 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
     if (tid == 0) {
         tile_stats[tile] = make_uint2(H, total >> 16);
         tile_count[tile] = n_out;
+        if (run_count) run_count[tile] = H;
     }
     if (n_out > slot) {
         if (tid == 0) atomicOr(err, ST_TABLE_FULL);
         return;
-    }
-    // kept runs' input keys in run order, at the tile's own offset of
-    // kept_slot (a tile has at most as many kept runs as keys)
-    if (list_kept) {
-        uint32_t kbase = 0;
-        const uint32_t lt = (1u << lane) - 1u;
-#pragma unroll
-        for (int j = 0; j < kRunsPerThread; j++) {
-            if ((uint32_t)(j * kRunThreads) >= H) break;
-            uint32_t pre = 0, tot = 0;
-#pragma unroll
-            for (int w = 0; w < kRunThreads / 32; w++) {
-                const uint32_t c = wkept[j * 8 + w];
-                pre += w < warp ? c : 0u;
-                tot += c;
-            }
-            if (nout[j]) kept_slot[start + kbase + pre + __popc(kbal[j] & lt)] = tk[rp(hp[tid + j * kRunThreads])];
-            kbase += tot;
-        }
-        if (tid == 0) kept_count[tile] = kbase;
     }
     const uint64_t toff = tile * (uint64_t)slot;
     // a tile's outputs fill [toff, toff + n_out): for 1-word keys that fit,
@@ -396,13 +351,16 @@ __global__ void runs_compact_kernel(const uint64_t* __restrict__ k, const uint32
     }
 }
 
-// Tile t's cnt[t] kept keys (at t * kRunTile) move to off[t].
-__global__ void kept_compact_kernel(const uint64_t* __restrict__ slot, const uint32_t* __restrict__ cnt,
-                                    const uint64_t* __restrict__ off, uint64_t* __restrict__ out) {
+// Tile t's cnt[t] runs (keys of nw words and lengths, at t * kRunTile) move
+// to off[t].
+__global__ void run_list_compact_kernel(const uint64_t* __restrict__ kslot, const uint32_t* __restrict__ lslot,
+                                        const uint32_t* __restrict__ cnt, const uint64_t* __restrict__ off, int nw,
+                                        uint64_t* __restrict__ keys, uint32_t* __restrict__ lens) {
     const uint64_t t = blockIdx.x;
     const uint64_t src = t * (uint64_t)kRunTile, dst = off[t];
     const uint32_t m = cnt[t];
-    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) out[dst + i] = slot[src + i];
+    for (uint32_t i = threadIdx.x; i < m * nw; i += blockDim.x) keys[dst * nw + i] = kslot[src * nw + i];
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) lens[dst + i] = lslot[src + i];
 }
 
 // Sorted canonical keys -> both-strand keys of kept runs, sorted ascending.
@@ -411,8 +369,9 @@ __global__ void kept_compact_kernel(const uint64_t* __restrict__ slot, const uin
 template <int NW>
 void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, Buf<uint64_t>& out_keys,
                  Buf<uint32_t>& out_cnt, uint64_t* n_out, uint64_t* n_canon_runs, uint64_t* n_palin_runs,
-                 const uint64_t* spectrum, uint64_t n_spectrum, bool in_mixed, bool spec_mixed, KeptList* kept) {
-    if (kept && (NW != 1 || spectrum)) fail(MH_EUNSUPPORTED, "kept-run lists are for 1-word counting");
+                 const uint64_t* spectrum, const uint32_t* spectrum_len, uint64_t n_spectrum, bool in_mixed,
+                 bool spec_mixed, RunList* list) {
+    if (list && spectrum) fail(MH_EUNSUPPORTED, "run lists are made while counting");
     const int K1 = k + 1;
     const uint64_t tiles = ceil_div(n ? n : 1, kRunTile);
     // a tile's outputs: when every kept run has >= 2 keys or is a palindrome
@@ -431,31 +390,39 @@ void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, 
                   tiles, first.p);
         MH_LAUNCH(ctx, "runs_next_head", grid_for(ctx, tiles, 256), 256, 0, run_next_head_kernel, first.p, tiles, n,
                   next.p);
-        const size_t smem = sizeof(uint64_t) * kRunTilePad * NW + sizeof(uint32_t) * (2 * (kRunTile / 32) + 16 + 64) +
+        const size_t smem = sizeof(uint64_t) * kRunTilePad * NW + sizeof(uint32_t) * (2 * (kRunTile / 32) + 16) +
                             sizeof(uint16_t) * kRunTile +
                             (NW == 1 ? (sizeof(uint64_t) + sizeof(uint32_t)) * kRunTile : 0);
         auto kern = in_mixed ? runs_kernel<NW, true> : runs_kernel<NW, false>;
         MH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         Buf<uint2> tstats(ctx, tiles);
-        Buf<uint32_t> kcount(ctx, kept ? tiles : 1);
+        Buf<uint32_t> rcount(ctx, list ? tiles : 1);
+        Buf<uint32_t> rlen(ctx, list ? tiles * (uint64_t)kRunTile : 1);
         MH_LAUNCH_B(ctx, "runs", n * 8 * NW, (unsigned)tiles, kRunThreads, smem, kern, sorted, n, K1, d, spectrum,
-                    n_spectrum, spec_mixed, next.p, big_k.p, big_c.p, slot, tcount.p, tstats.p,
-                    kept ? kept->slot.p : nullptr, kcount.p, ctx->d_status);
-        if (kept) {
-            Buf<uint64_t> koff(ctx, tiles + 1);
-            exclusive_scan_u32(ctx, kcount.p, koff.p, tiles);
-            read_u64(ctx, koff.p + tiles, &kept->n, 1);
-            kept->keys = Buf<uint64_t>(ctx, kept->n ? kept->n : 1);
-            if (kept->n)
-                MH_LAUNCH(ctx, "runs_kept_compact", (unsigned)tiles, 256, 0, kept_compact_kernel, kept->slot.p,
-                          kcount.p, koff.p, kept->keys.p);
-            kept->slot.reset();
+                    spectrum_len, n_spectrum, spec_mixed, next.p, big_k.p, big_c.p, slot, tcount.p, tstats.p,
+                    list ? list->slot.p : nullptr, list ? rlen.p : nullptr, list ? rcount.p : nullptr,
+                    ctx->d_status);
+        if (list) {
+            Buf<uint64_t> roff(ctx, tiles + 1);
+            exclusive_scan_u32(ctx, rcount.p, roff.p, tiles);
+            read_u64(ctx, roff.p + tiles, &list->n, 1);
+            list->keys = Buf<uint64_t>(ctx, (list->n ? list->n : 1) * NW);
+            list->lens = Buf<uint32_t>(ctx, list->n ? list->n : 1);
+            if (list->n)
+                MH_LAUNCH(ctx, "run_list_compact", (unsigned)tiles, 256, 0, run_list_compact_kernel, list->slot.p,
+                          rlen.p, rcount.p, roff.p, NW, list->keys.p, list->lens.p);
+            list->slot.reset();
         }
         MH_LAUNCH(ctx, "runs_totals", grid_for(ctx, tiles, 256, 2), 256, 0, sum_tile_stats_kernel, tstats.p, tiles,
                   (unsigned long long*)totals.p);
         exclusive_scan_u32(ctx, tcount.p, toff.p, tiles);
         read_u64(ctx, toff.p + tiles, &S, 1);
         read_u64(ctx, totals.p, tot, 2);
+    }
+    if (list && !list->keys.p) {  // no input: an empty spectrum
+        list->keys = Buf<uint64_t>(ctx, NW);
+        list->lens = Buf<uint32_t>(ctx, 1);
+        list->slot.reset();
     }
     *n_out = S;
     *n_canon_runs = tot[0];
@@ -480,11 +447,14 @@ void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, 
 }
 
 template void expand_runs<1>(mh_ctx*, const uint64_t*, uint64_t, int, int, Buf<uint64_t>&, Buf<uint32_t>&, uint64_t*,
-                             uint64_t*, uint64_t*, const uint64_t*, uint64_t, bool, bool, KeptList*);
+                             uint64_t*, uint64_t*, const uint64_t*, const uint32_t*, uint64_t, bool, bool,
+                             RunList*);
 template void expand_runs<2>(mh_ctx*, const uint64_t*, uint64_t, int, int, Buf<uint64_t>&, Buf<uint32_t>&, uint64_t*,
-                             uint64_t*, uint64_t*, const uint64_t*, uint64_t, bool, bool, KeptList*);
+                             uint64_t*, uint64_t*, const uint64_t*, const uint32_t*, uint64_t, bool, bool,
+                             RunList*);
 template void expand_runs<4>(mh_ctx*, const uint64_t*, uint64_t, int, int, Buf<uint64_t>&, Buf<uint32_t>&, uint64_t*,
-                             uint64_t*, uint64_t*, const uint64_t*, uint64_t, bool, bool, KeptList*);
+                             uint64_t*, uint64_t*, const uint64_t*, const uint32_t*, uint64_t, bool, bool,
+                             RunList*);
 
 template <int NW>
 void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out) {
@@ -506,19 +476,18 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
                     (extract_canonical_kernel<NW, kMixed>), reads->packed, reads->frag_offs, woff.p, F, k, keys.p);
     woff.reset();
     bool in_alt = radix_sort_spread<NW>(ctx, keys.p, alt.p, n);
-    Buf<uint64_t>& spec = in_alt ? alt : keys;
+    Buf<uint64_t>& sorted = in_alt ? alt : keys;
     Buf<uint64_t>& other = in_alt ? keys : alt;
     Buf<uint64_t> sk;
     Buf<uint32_t> sc;
     uint64_t S = 0, runs = 0, palins = 0;
-    // 1-word keys: the kept canonical keys (mixed, ascending) are listed too,
-    // in the free sort buffer
-    KeptList kept;
-    constexpr bool kList = kMixed && NW == 1;
-    if (kList) kept.slot = std::move(other);
+    // every run (mixed key, length) is listed too, in the free sort buffer:
+    // the spectrum the mercy step looks counts up in
+    RunList list;
+    list.slot = std::move(other);
     other.reset();
-    expand_runs<NW>(ctx, spec.p, n, k, d, sk, sc, &S, &runs, &palins, nullptr, 0, kMixed, false,
-                    kList ? &kept : nullptr);
+    expand_runs<NW>(ctx, sorted.p, n, k, d, sk, sc, &S, &runs, &palins, nullptr, nullptr, 0, kMixed, false, &list);
+    sorted.reset();
     sync_and_check(ctx);
     out->k = k;
     out->nw = NW;
@@ -528,13 +497,10 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
     out->n_distinct = 2 * runs - palins;
     out->keys = sk.release();
     out->counts = sc.release();
-    out->n_spectrum = n;
+    out->n_spectrum = list.n;
     out->spectrum_mixed = kMixed;
-    out->spectrum = spec.release();
-    if (kList) {
-        out->n_canon = kept.n;
-        out->canon = kept.keys.release();
-    }
+    out->spectrum = list.keys.release();
+    out->spectrum_len = list.lens.release();
 }
 
 template void count_kmers<1>(mh_ctx*, const mh_reads*, int, int, mh_kmers*);

@@ -89,15 +89,14 @@ struct mh_kmers {
     uint64_t n = 0;
     uint64_t* keys = nullptr;   // n * nw
     uint32_t* counts = nullptr; // n
-    // counting handles: the sorted canonical spectrum (min(x, rc x) of every
-    // window, with repeats) kept for the mercy counts
-    uint64_t* spectrum = nullptr;
+    // counting handles: the spectrum, every distinct canonical (k+1)-mer
+    // (min(x, rc x)) as a mix_key image, ascending, with the number of
+    // windows it has (before doubling for a palindrome); the mercy step
+    // looks counts up in it
+    uint64_t* spectrum = nullptr;      // n_spectrum * nw
+    uint32_t* spectrum_len = nullptr;  // n_spectrum
     uint64_t n_spectrum = 0;
-    bool spectrum_mixed = false;  // spectrum holds mix_bij(canonical), sorted
-    // counting handles with 1-word keys: mix_bij of every solid canonical
-    // key, ascending (the solidity set of the mercy walk)
-    uint64_t* canon = nullptr;
-    uint64_t n_canon = 0;
+    bool spectrum_mixed = false;
     uint64_t n_kmers = 0, n_distinct = 0;
     mh_ctx* ctx = nullptr;
 };
@@ -595,10 +594,6 @@ void exclusive_scan_u64(mh_ctx* ctx, const uint64_t* in, uint64_t* out, uint64_t
 void exclusive_scan_u32(mh_ctx* ctx, const uint32_t* in, uint64_t* out, uint64_t n);
 
 // ------------------------------------------------- counting stages
-// Sorted canonical spectrum -> solid (k+1)-mers, both strands, sorted.
-// Defined in mh_count.cu, used by mercy too (d = 1, counts looked up).
-// in_mixed: `sorted` holds mix_bij of the canonical keys (1-word keys only);
-// spec_mixed: likewise for the spectrum.
 // Merge of sorted runs [bounds[i], bounds[i+1]) of keys (and payload, when
 // vals) into one sorted sequence; returns true when the result is in alt/valt.
 template <int NW>
@@ -616,19 +611,24 @@ void walk_contigs(mh_ctx* ctx, const mh_kmers* solid, const mh_kmers* mercy, uin
 void pack_with_contigs(mh_ctx* ctx, const uint8_t* d_ascii, uint64_t n_bases, const uint64_t* d_offs,
                        uint64_t n_reads, const mh_contigs* contigs, uint32_t copies, mh_reads* out);
 
-// Optional output of expand_runs in counting mode (1-word keys): the kept
-// runs' input keys, in input order.  `slot` is scratch of >= n words, freed
-// once the list is compacted.
-struct KeptList {
+// Optional output of expand_runs in counting mode: every run's input key
+// and length, in input order.  `slot` is scratch of >= n keys, freed once
+// the list is compacted.
+struct RunList {
     Buf<uint64_t> slot;
     Buf<uint64_t> keys;
+    Buf<uint32_t> lens;
     uint64_t n = 0;
 };
 
+// Sorted canonical keys -> solid (k+1)-mers, both strands, sorted.  Defined
+// in mh_count.cu, used by mercy too (d = 1, counts looked up in the
+// spectrum).  in_mixed: `sorted` holds mix_key images of the canonical keys;
+// spec_mixed: likewise for the spectrum.
 template <int NW>
 void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, Buf<uint64_t>& out_keys,
                  Buf<uint32_t>& out_cnt, uint64_t* n_out, uint64_t* n_canon_runs, uint64_t* n_palin_runs,
-                 const uint64_t* spectrum, uint64_t n_spectrum, bool in_mixed = false, bool spec_mixed = false,
-                 KeptList* kept = nullptr);
+                 const uint64_t* spectrum, const uint32_t* spectrum_len, uint64_t n_spectrum, bool in_mixed = false,
+                 bool spec_mixed = false, RunList* list = nullptr);
 
 }  // namespace mh

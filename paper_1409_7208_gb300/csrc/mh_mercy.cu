@@ -21,9 +21,10 @@
 //   walk     thread per hit: step forward to the next solid window q; if
 //            q > p+1 and q has no indegree, the windows p+1..q-1 are emitted
 //            (canonical keys).  Solidity of 1-word keys: a search of the
-//            counting handle's solid canonical keys, ascending as mix_bij
-//            images (so evenly spread), through a bucket index on their top
-//            bits; wider keys: a hash set of the canonical solid keys.
+//            counting spectrum (distinct canonical keys, ascending as mix_bij
+//            images, so evenly spread, with their run lengths) through a
+//            bucket index on their top bits; wider keys: a hash set of the
+//            canonical solid keys.
 //   finish   sort + dedup of the candidates, counts looked up in the
 //            counting spectrum, both strands, sorted.
 #include "mh_internal.cuh"
@@ -248,9 +249,9 @@ __device__ __forceinline__ uint32_t ends_find(const Slot<NW>* __restrict__ table
 // holding the key itself, empty = all ones (never canonical: the reverse
 // complement of T...T is A...A, which is smaller); wider keys use Slot
 // (32-bit tag + key).
-// Bucket index over the ascending mixed solid keys: off[b] = first index
-// whose top `bits` bits are >= b, for b = 0..2^bits (thread per key; each
-// bucket boundary is written by exactly one thread).
+// Bucket index over the ascending mixed spectrum keys (1-word): off[b] =
+// first index whose top `bits` bits are >= b, for b = 0..2^bits (thread per
+// key; each bucket boundary is written by exactly one thread).
 __global__ void canon_index_kernel(const uint64_t* __restrict__ canon, uint64_t n, int bits,
                                    uint64_t* __restrict__ off) {
     const int sh = 64 - bits;
@@ -264,17 +265,18 @@ __global__ void canon_index_kernel(const uint64_t* __restrict__ canon, uint64_t 
     }
 }
 
-// Is the mixed key m in the ascending list (bucket index off, `bits` bits)?
-__device__ __forceinline__ bool canon_has(const uint64_t* __restrict__ canon, const uint64_t* __restrict__ off,
-                                          int bits, uint64_t m) {
+// Run length of the mixed key m in the ascending spectrum (bucket index
+// off over `bits` top bits), 0 if absent.
+__device__ __forceinline__ uint32_t spec_find(const uint64_t* __restrict__ spec, const uint32_t* __restrict__ len,
+                                              const uint64_t* __restrict__ off, int bits, uint64_t m) {
     const uint64_t b = m >> (64 - bits);
     uint64_t i = off[b];
     const uint64_t e = off[b + 1];
     for (; i < e; i++) {
-        const uint64_t v = canon[i];
-        if (v >= m) return v == m;
+        const uint64_t v = spec[i];
+        if (v >= m) return v == m ? len[i] : 0u;
     }
-    return false;
+    return 0u;
 }
 
 template <int NW>
@@ -359,15 +361,17 @@ __global__ void __launch_bounds__(256) mercy_probe_kernel(const uint32_t* __rest
 
 // Walk from each hit to the next solid window; emit the gap if it qualifies.
 // MIXED: candidates out as mix_key images; 1-word keys then take solidity
-// from the ascending mixed solid keys `canon` with its bucket index, wider
-// keys (and unmixed handles) from the hash set `solid`.
+// from the counting spectrum (run length, doubled for a palindrome, >= d)
+// through its bucket index, wider keys (and unmixed handles) from the hash
+// set `solid`.
 template <int NW, bool MIXED>
 __global__ void __launch_bounds__(256) mercy_walk_kernel(const uint32_t* __restrict__ packed,
                                                          const ulonglong2* __restrict__ hits, uint64_t n_hits, int k,
                                                          const Slot<NW>* __restrict__ ends, uint64_t ends_mask,
                                                          const Slot<NW>* __restrict__ solid, uint64_t solid_mask,
-                                                         const uint64_t* __restrict__ canon,
-                                                         const uint64_t* __restrict__ canon_off, int canon_bits,
+                                                         const uint64_t* __restrict__ spec,
+                                                         const uint32_t* __restrict__ spec_len,
+                                                         const uint64_t* __restrict__ spec_off, int spec_bits, int d,
                                                          uint64_t* __restrict__ out, uint64_t out_cap,
                                                          unsigned long long* __restrict__ counter) {
     const int K1 = k + 1;
@@ -382,9 +386,10 @@ __global__ void __launch_bounds__(256) mercy_walk_kernel(const uint32_t* __restr
             Key<NW> r = key_rc<NW>(x, K1);
             const Key<NW> c = key_less<NW>(r, x) ? r : x;
             bool present;
-            if constexpr (MIXED && NW == 1)
-                present = canon_has(canon, canon_off, canon_bits, mix_bij(c.w[0]));
-            else
+            if constexpr (MIXED && NW == 1) {
+                const uint32_t len = spec_find(spec, spec_len, spec_off, spec_bits, mix_bij(c.w[0]));
+                present = (uint64_t)len * (key_eq<NW>(r, x) ? 2 : 1) >= (uint64_t)d;
+            } else
                 present = table_has<NW>(solid, solid_mask, c);
             if (present) {
                 y = x;
@@ -446,18 +451,17 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
     // keys with a bucket index (4 to 8 keys a bucket); wider keys a hash set
     // of the canonical solid keys, load <= 1/2 (<= 0.61 if all palindromes)
     const bool mixed = solid->spectrum_mixed;
-    if (NW == 1 && mixed && !solid->canon && S) fail(MH_EINVAL, "the solid handle must come from mh_count_kmers");
     Buf<Slot<NW>> sset;
     uint64_t scap = 1;
-    Buf<uint64_t> canon_off;
-    int canon_bits = 1;
+    Buf<uint64_t> spec_off;
+    int spec_bits = 1;
     if (NW == 1 && mixed) {
-        while (canon_bits < 40 && (2ull << canon_bits) * 4 <= solid->n_canon) canon_bits++;
-        canon_off = Buf<uint64_t>(ctx, (1ull << canon_bits) + 1);
-        canon_off.zero();
-        if (solid->n_canon)
-            MH_LAUNCH(ctx, "mercy_canon_index", grid_for(ctx, solid->n_canon, 256), 256, 0, canon_index_kernel,
-                      solid->canon, solid->n_canon, canon_bits, canon_off.p);
+        while (spec_bits < 40 && (2ull << spec_bits) * 4 <= solid->n_spectrum) spec_bits++;
+        spec_off = Buf<uint64_t>(ctx, (1ull << spec_bits) + 1);
+        spec_off.zero();
+        if (solid->n_spectrum)
+            MH_LAUNCH(ctx, "mercy_spectrum_index", grid_for(ctx, solid->n_spectrum, 256), 256, 0,
+                      canon_index_kernel, solid->spectrum, solid->n_spectrum, spec_bits, spec_off.p);
     } else {
         scap = next_pow2(std::max<uint64_t>(S + S / 2, 64));
         sset = Buf<Slot<NW>>(ctx, scap);
@@ -493,7 +497,8 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
         if (n_hits)
             MH_LAUNCH(ctx, "mercy_walk", grid_for(ctx, n_hits, 256, 8), 256, 0,
                       (mixed ? mercy_walk_kernel<NW, true> : mercy_walk_kernel<NW, false>), reads->packed,
-                      hits.p, n_hits, k, table.p, cap - 1, sset.p, scap - 1, solid->canon, canon_off.p, canon_bits,
+                      hits.p, n_hits, k, table.p, cap - 1, sset.p, scap - 1, solid->spectrum, solid->spectrum_len,
+                      spec_off.p, spec_bits, solid->d,
                       cand.p, out_cap, (unsigned long long*)(stats.p + 1));
         read_u64(ctx, stats.p + 1, &n_cand, 1);
         if (n_cand <= out_cap) break;
@@ -501,7 +506,7 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
     }
     hits.reset();
     sset.reset();
-    canon_off.reset();
+    spec_off.reset();
     table.reset();
     Buf<uint64_t> alt(ctx, (n_cand ? n_cand : 1) * NW);
     bool in_alt = mixed ? radix_sort_spread<NW>(ctx, cand.p, alt.p, n_cand)
@@ -510,8 +515,8 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
     Buf<uint64_t> mk;
     Buf<uint32_t> mc;
     uint64_t M = 0, runs = 0, palins = 0;
-    expand_runs<NW>(ctx, sorted.p, n_cand, k, 1, mk, mc, &M, &runs, &palins, solid->spectrum, solid->n_spectrum,
-                    mixed, solid->spectrum_mixed);
+    expand_runs<NW>(ctx, sorted.p, n_cand, k, 1, mk, mc, &M, &runs, &palins, solid->spectrum, solid->spectrum_len,
+                    solid->n_spectrum, mixed, solid->spectrum_mixed);
     sync_and_check(ctx);
     out->k = k;
     out->nw = NW;
