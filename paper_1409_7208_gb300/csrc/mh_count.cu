@@ -15,6 +15,9 @@
 //             next head, solid filter, outputs placed by decoupled look-back
 //   expand    each solid canonical key -> itself and its reverse complement
 //   sort      key-value LSD radix -> solid table in ascending key order
+#include <cstdlib>
+#include <vector>
+
 #include "mh_internal.cuh"
 
 namespace mh {
@@ -49,6 +52,81 @@ __global__ void __launch_bounds__(256) extract_canonical_kernel(const uint32_t* 
             Key<NW> c = key_less<NW>(r, x) ? r : x;
             if constexpr (MIXED) c = mix_key<NW>(c);
             store_key<NW>(out, w0 + i, c);
+        }
+    }
+}
+
+// Buckets of the mixed canonical keys: the top `bb` bits of the top word.
+template <int NW>
+__device__ __forceinline__ uint32_t key_bucket(const Key<NW>& m, int bb) {
+    return bb ? (uint32_t)(m.w[NW - 1] >> (64 - bb)) : 0u;
+}
+
+// Bucketed extraction: fragments in tasks of kTaskFrags, a warp per task.
+// A first pass counts the windows of every (bucket, task); after a scan of
+// each bucket's row, a bucket's pass writes its keys at exact offsets, in
+// task order, without atomics.
+constexpr int kTaskFrags = 64;
+
+template <int NW>
+__global__ void __launch_bounds__(256) task_hist_kernel(const uint32_t* __restrict__ packed,
+                                                        const uint64_t* __restrict__ frag_offs, uint64_t n_frags,
+                                                        int k, int bb, uint64_t n_tasks, uint32_t* __restrict__ cnt) {
+    __shared__ uint32_t h[8][64];  // per warp, up to 64 buckets
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const int K1 = k + 1, nb = 1 << bb;
+    for (uint64_t t = warp; t < n_tasks; t += n_warps) {
+        for (int i = lane; i < nb; i += 32) h[wib][i] = 0;
+        __syncwarp();
+        const uint64_t f1 = (t + 1) * kTaskFrags < n_frags ? (t + 1) * kTaskFrags : n_frags;
+        for (uint64_t f = t * kTaskFrags; f < f1; f++) {
+            const uint64_t b = frag_offs[f], L = frag_offs[f + 1] - b;
+            const uint64_t nwin = L > (uint64_t)k ? L - k : 0;
+            for (uint64_t i = lane; i < nwin; i += 32) {
+                const Key<NW> x = load_window<NW>(packed, b + i, K1);
+                const Key<NW> r = key_rc<NW>(x, K1);
+                atomicAdd(&h[wib][key_bucket<NW>(mix_key<NW>(key_less<NW>(r, x) ? r : x), bb)], 1u);
+            }
+        }
+        __syncwarp();
+        for (int i = lane; i < nb; i += 32) cnt[(uint64_t)i * n_tasks + t] = h[wib][i];
+        __syncwarp();
+    }
+}
+
+// The mixed canonical keys of bucket `bk`, task t's at off[t] onwards.
+template <int NW>
+__global__ void __launch_bounds__(256) extract_bucket_kernel(const uint32_t* __restrict__ packed,
+                                                             const uint64_t* __restrict__ frag_offs,
+                                                             uint64_t n_frags, int k, int bb, uint32_t bk,
+                                                             uint64_t n_tasks, const uint64_t* __restrict__ off,
+                                                             uint64_t* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const int K1 = k + 1;
+    for (uint64_t t = warp; t < n_tasks; t += n_warps) {
+        uint64_t at = off[t];
+        const uint64_t f1 = (t + 1) * kTaskFrags < n_frags ? (t + 1) * kTaskFrags : n_frags;
+        for (uint64_t f = t * kTaskFrags; f < f1; f++) {
+            const uint64_t b = frag_offs[f], L = frag_offs[f + 1] - b;
+            const uint64_t nwin = L > (uint64_t)k ? L - k : 0;
+            for (uint64_t base = 0; base < nwin; base += 32) {
+                const uint64_t i = base + lane;
+                Key<NW> c;
+                bool keep = false;
+                if (i < nwin) {
+                    const Key<NW> x = load_window<NW>(packed, b + i, K1);
+                    const Key<NW> r = key_rc<NW>(x, K1);
+                    c = mix_key<NW>(key_less<NW>(r, x) ? r : x);
+                    keep = key_bucket<NW>(c, bb) == bk;
+                }
+                const uint32_t m = __ballot_sync(0xFFFFFFFFu, keep);
+                if (keep) store_key<NW>(out, at + __popc(m & ((1u << lane) - 1u)), c);
+                at += __popc(m);
+            }
         }
     }
 }
@@ -456,6 +534,26 @@ template void expand_runs<4>(mh_ctx*, const uint64_t*, uint64_t, int, int, Buf<u
                              uint64_t*, uint64_t*, const uint64_t*, const uint32_t*, uint64_t, bool, bool,
                              RunList*);
 
+// Buckets of the mixed canonical keys to count one at a time (0 = all at
+// once): with an HBM budget, enough that one bucket's working set (keys,
+// sort buffer, run slots: about 24 nw + 12 bytes a window) takes at most 60%
+// of the budget still free (up to 64 buckets).  MH_COUNT_BUCKET_BITS (0..6)
+// forces it (tests).
+static int count_bucket_bits(mh_ctx* ctx, uint64_t n, int nw) {
+    static const int forced = [] {
+        const char* e = std::getenv("MH_COUNT_BUCKET_BITS");
+        const int v = e ? std::atoi(e) : -1;
+        return v >= 0 && v <= 6 ? v : -1;
+    }();
+    if (forced >= 0) return forced;
+    if (!ctx->budget || !n) return 0;
+    const double per = 24.0 * nw + 12.0;
+    const double avail = ctx->budget > ctx->in_use ? (double)(ctx->budget - ctx->in_use) : 0.0;
+    int bb = 0;
+    while (bb < 6 && (double)n / (double)(1ull << bb) * 1.05 * per > 0.6 * avail) bb++;
+    return bb;
+}
+
 template <int NW>
 void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out) {
     const uint64_t F = reads->n_frags;
@@ -470,37 +568,146 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
     // keys are sorted as mix_key images: their evenly spread top bits let
     // the sort run its passes over the top ceil(log2 n) bits only
     constexpr bool kMixed = true;
-    Buf<uint64_t> keys(ctx, (n ? n : 1) * NW), alt(ctx, (n ? n : 1) * NW);
-    if (n)
-        MH_LAUNCH_B(ctx, "extract_canonical", reads->n_packed / 4 + n * 8 * NW, grid_for(ctx, F * 32, 256, 8), 256, 0,
-                    (extract_canonical_kernel<NW, kMixed>), reads->packed, reads->frag_offs, woff.p, F, k, keys.p);
-    woff.reset();
-    bool in_alt = radix_sort_spread<NW>(ctx, keys.p, alt.p, n);
-    Buf<uint64_t>& sorted = in_alt ? alt : keys;
-    Buf<uint64_t>& other = in_alt ? keys : alt;
-    Buf<uint64_t> sk;
-    Buf<uint32_t> sc;
-    uint64_t S = 0, runs = 0, palins = 0;
-    // every run (mixed key, length) is listed too, in the free sort buffer:
-    // the spectrum the mercy step looks counts up in
-    RunList list;
-    list.slot = std::move(other);
-    other.reset();
-    expand_runs<NW>(ctx, sorted.p, n, k, d, sk, sc, &S, &runs, &palins, nullptr, nullptr, 0, kMixed, false, &list);
-    sorted.reset();
-    sync_and_check(ctx);
     out->k = k;
     out->nw = NW;
     out->d = d;
-    out->n = S;
     out->n_kmers = 2 * n;
-    out->n_distinct = 2 * runs - palins;
+    out->spectrum_mixed = kMixed;
+    const int bb = count_bucket_bits(ctx, n, NW);
+    if (bb == 0) {
+        Buf<uint64_t> keys(ctx, (n ? n : 1) * NW), alt(ctx, (n ? n : 1) * NW);
+        if (n)
+            MH_LAUNCH_B(ctx, "extract_canonical", reads->n_packed / 4 + n * 8 * NW, grid_for(ctx, F * 32, 256, 8),
+                        256, 0, (extract_canonical_kernel<NW, kMixed>), reads->packed, reads->frag_offs, woff.p, F, k,
+                        keys.p);
+        woff.reset();
+        bool in_alt = radix_sort_spread<NW>(ctx, keys.p, alt.p, n);
+        Buf<uint64_t>& sorted = in_alt ? alt : keys;
+        Buf<uint64_t>& other = in_alt ? keys : alt;
+        Buf<uint64_t> sk;
+        Buf<uint32_t> sc;
+        uint64_t S = 0, runs = 0, palins = 0;
+        // every run (mixed key, length) is listed too, in the free sort buffer:
+        // the spectrum the mercy step looks counts up in
+        RunList list;
+        list.slot = std::move(other);
+        other.reset();
+        expand_runs<NW>(ctx, sorted.p, n, k, d, sk, sc, &S, &runs, &palins, nullptr, nullptr, 0, kMixed, false,
+                        &list);
+        sorted.reset();
+        sync_and_check(ctx);
+        out->n = S;
+        out->n_distinct = 2 * runs - palins;
+        out->keys = sk.release();
+        out->counts = sc.release();
+        out->n_spectrum = list.n;
+        out->spectrum = list.keys.release();
+        out->spectrum_len = list.lens.release();
+        return;
+    }
+    // Out of core: one bucket of the mixed canonical keys at a time (the
+    // paper partitions its sort by k-mer prefix blocks the same way, Sec. 2
+    // second paragraph).  Every window is extracted once per bucket and kept
+    // if its key falls in it; each bucket is sorted (skipping its constant
+    // top bits) and counted alone.  The spectrum is the buckets' spectra in
+    // bucket order; the solid tables (both strands, real key order) of the
+    // buckets are merged.
+    woff.reset();
+    const uint32_t nb = 1u << bb;
+    const uint64_t n_tasks = ceil_div(F ? F : 1, (uint64_t)kTaskFrags);
+    Buf<uint32_t> tcnt(ctx, nb * n_tasks);
+    if (F)
+        MH_LAUNCH(ctx, "bucket_hist", grid_for(ctx, n_tasks * 32, 256, 8), 256, 0, task_hist_kernel<NW>,
+                  reads->packed, reads->frag_offs, F, k, bb, n_tasks, tcnt.p);
+    else
+        tcnt.zero();
+    std::vector<uint64_t> hist(nb, 0);
+    std::vector<Buf<uint64_t>> toff;
+    for (uint32_t b = 0; b < nb; b++) {
+        toff.emplace_back(ctx, n_tasks + 1);
+        exclusive_scan_u32(ctx, tcnt.p + (uint64_t)b * n_tasks, toff[b].p, n_tasks);
+    }
+    for (uint32_t b = 0; b < nb; b++) read_u64(ctx, toff[b].p + n_tasks, &hist[b], 1);
+    tcnt.reset();
+    std::vector<Buf<uint64_t>> part_k, part_sk;
+    std::vector<Buf<uint32_t>> part_l, part_sc;
+    std::vector<uint64_t> part_n, part_S;
+    uint64_t runs_tot = 0, palins_tot = 0;
+    for (uint32_t b = 0; b < nb; b++) {
+        const uint64_t m = hist[b];
+        Buf<uint64_t> keys(ctx, (m ? m : 1) * NW), alt(ctx, (m ? m : 1) * NW);
+        if (m)
+            MH_LAUNCH_B(ctx, "extract_bucket", reads->n_packed / 4 + m * 8 * NW, grid_for(ctx, n_tasks * 32, 256, 8),
+                        256, 0, extract_bucket_kernel<NW>, reads->packed, reads->frag_offs, F, k, bb, b, n_tasks,
+                        toff[b].p, keys.p);
+        toff[b].reset();
+        const bool in_alt = radix_sort_spread<NW>(ctx, keys.p, alt.p, m, bb);
+        Buf<uint64_t>& sorted = in_alt ? alt : keys;
+        Buf<uint64_t>& other = in_alt ? keys : alt;
+        Buf<uint64_t> sk;
+        Buf<uint32_t> sc;
+        uint64_t S = 0, runs = 0, palins = 0;
+        RunList list;
+        list.slot = std::move(other);
+        other.reset();
+        expand_runs<NW>(ctx, sorted.p, m, k, d, sk, sc, &S, &runs, &palins, nullptr, nullptr, 0, kMixed, false,
+                        &list);
+        sorted.reset();
+        runs_tot += runs;
+        palins_tot += palins;
+        part_k.push_back(std::move(list.keys));
+        part_l.push_back(std::move(list.lens));
+        part_n.push_back(list.n);
+        part_sk.push_back(std::move(sk));
+        part_sc.push_back(std::move(sc));
+        part_S.push_back(S);
+    }
+    // spectrum: the buckets' spectra back to back
+    uint64_t n_spec = 0, S_tot = 0;
+    for (uint32_t b = 0; b < nb; b++) {
+        n_spec += part_n[b];
+        S_tot += part_S[b];
+    }
+    Buf<uint64_t> spec(ctx, (n_spec ? n_spec : 1) * NW);
+    Buf<uint32_t> spec_len(ctx, n_spec ? n_spec : 1);
+    for (uint64_t b = 0, o = 0; b < nb; o += part_n[b], b++) {
+        if (part_n[b]) {
+            MH_CUDA(cudaMemcpyAsync(spec.p + o * NW, part_k[b].p, part_n[b] * NW * 8, cudaMemcpyDeviceToDevice,
+                                    ctx->stream));
+            MH_CUDA(cudaMemcpyAsync(spec_len.p + o, part_l[b].p, part_n[b] * 4, cudaMemcpyDeviceToDevice,
+                                    ctx->stream));
+        }
+        part_k[b].reset();
+        part_l[b].reset();
+    }
+    // solid: the buckets' tables back to back, then merged
+    Buf<uint64_t> sk(ctx, (S_tot ? S_tot : 1) * NW), sk2(ctx, (S_tot ? S_tot : 1) * NW);
+    Buf<uint32_t> sc(ctx, S_tot ? S_tot : 1), sc2(ctx, S_tot ? S_tot : 1);
+    std::vector<uint64_t> bounds(1, 0);
+    for (uint64_t b = 0, o = 0; b < nb; o += part_S[b], b++) {
+        if (part_S[b]) {
+            MH_CUDA(cudaMemcpyAsync(sk.p + o * NW, part_sk[b].p, part_S[b] * NW * 8, cudaMemcpyDeviceToDevice,
+                                    ctx->stream));
+            MH_CUDA(cudaMemcpyAsync(sc.p + o, part_sc[b].p, part_S[b] * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+        part_sk[b].reset();
+        part_sc[b].reset();
+        bounds.push_back(o + part_S[b]);
+    }
+    if (merge_runs<NW>(ctx, sk.p, sk2.p, sc.p, sc2.p, bounds)) {
+        std::swap(sk, sk2);
+        std::swap(sc, sc2);
+    }
+    sk2.reset();
+    sc2.reset();
+    sync_and_check(ctx);
+    out->n = S_tot;
+    out->n_distinct = 2 * runs_tot - palins_tot;
     out->keys = sk.release();
     out->counts = sc.release();
-    out->n_spectrum = list.n;
-    out->spectrum_mixed = kMixed;
-    out->spectrum = list.keys.release();
-    out->spectrum_len = list.lens.release();
+    out->n_spectrum = n_spec;
+    out->spectrum = spec.release();
+    out->spectrum_len = spec_len.release();
 }
 
 template void count_kmers<1>(mh_ctx*, const mh_reads*, int, int, mh_kmers*);

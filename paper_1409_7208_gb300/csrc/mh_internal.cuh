@@ -585,8 +585,10 @@ bool radix_sort(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint
 // k-mers): LSD passes over the top P = ceil(log2 n) + 8 bits only (whole
 // digits), then the rare groups of distinct keys sharing those bits are put
 // in order.  Returns true if the result is in alt.
+// Sort of mix_key images: passes over the top bits only, then a fix-up of
+// keys that share them.  The top `skip` bits must be equal in every key.
 template <int NW>
-bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n);
+bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n, int skip = 0);
 
 // ---------------------------------------------------------------- scans
 // out[i] = sum of in[0..i-1] for i in [0, n]; out has n+1 entries.

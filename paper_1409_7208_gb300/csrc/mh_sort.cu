@@ -435,13 +435,14 @@ static int spread_bits(uint64_t n) {
 }
 
 template <int NW>
-bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n) {
+bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n, int skip) {
     using F = Fix<NW>;
     const int P = spread_bits(n);
     const int bits = 64 * NW;
-    if (n <= 1 || P >= 64) return radix_sort<NW>(ctx, keys, alt, nullptr, nullptr, n, 0, bits);
-    const int lo = 64 - P;  // within the top word
-    const bool in_alt = radix_sort<NW>(ctx, keys, alt, nullptr, nullptr, n, bits - P, bits);
+    if (n <= 1 || P + skip >= 64) return radix_sort<NW>(ctx, keys, alt, nullptr, nullptr, n, 0, bits - skip);
+    // the top `skip` bits are equal in every key: passes over the P bits below
+    const int lo = 64 - skip - P;  // within the top word
+    const bool in_alt = radix_sort<NW>(ctx, keys, alt, nullptr, nullptr, n, bits - skip - P, bits - skip);
     uint64_t* k = in_alt ? alt : keys;
     uint64_t* other = in_alt ? keys : alt;
     const uint64_t cap = std::max<uint64_t>(1 << 16, n / 64);
@@ -453,7 +454,7 @@ bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n) {
     read_u64(ctx, cnt.p, &n_big, 1);
     if (n_big > cap) {
         // far more long or crowded groups than evenly spread keys give: sort fully
-        return in_alt != radix_sort<NW>(ctx, k, other, nullptr, nullptr, n, 0, bits);
+        return in_alt != radix_sort<NW>(ctx, k, other, nullptr, nullptr, n, 0, bits - skip);
     }
     if (n_big) {
         Buf<ulonglong2> rest(ctx, n_big);
@@ -468,7 +469,8 @@ bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n) {
             sync_and_check(ctx);
             for (const ulonglong2& seg : h) {
                 const uint64_t len = seg.y - seg.x;
-                if (radix_sort<NW>(ctx, k + seg.x * NW, other + seg.x * NW, nullptr, nullptr, len, 0, bits - P))
+                if (radix_sort<NW>(ctx, k + seg.x * NW, other + seg.x * NW, nullptr, nullptr, len, 0,
+                                   bits - skip - P))
                     MH_CUDA(cudaMemcpyAsync(k + seg.x * NW, other + seg.x * NW, len * 8 * NW, cudaMemcpyDeviceToDevice,
                                             ctx->stream));
             }
@@ -477,9 +479,9 @@ bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n) {
     return in_alt;
 }
 
-template bool radix_sort_spread<1>(mh_ctx*, uint64_t*, uint64_t*, uint64_t);
-template bool radix_sort_spread<2>(mh_ctx*, uint64_t*, uint64_t*, uint64_t);
-template bool radix_sort_spread<4>(mh_ctx*, uint64_t*, uint64_t*, uint64_t);
+template bool radix_sort_spread<1>(mh_ctx*, uint64_t*, uint64_t*, uint64_t, int);
+template bool radix_sort_spread<2>(mh_ctx*, uint64_t*, uint64_t*, uint64_t, int);
+template bool radix_sort_spread<4>(mh_ctx*, uint64_t*, uint64_t*, uint64_t, int);
 
 // ------------------------------------------------------------------ scans
 constexpr int kScanThreads = 256;

@@ -4,7 +4,9 @@ multi-chunk path (several look-back chains per pass, digit offsets carried
 between chunks; 1 or 3 tiles per chunk), and the count sort's fix-up of
 keys sharing their top bits (passes over the top 8, 16 or 24 bits only, so
 that groups of every size occur: a few keys sorted by one thread, tens to
-thousands by a warp or a CTA, and crowded groups by the segment fallback)."""
+thousands by a warp or a CTA, and crowded groups by the segment fallback),
+and the out-of-core count (2 or 16 buckets of keys counted one at a time,
+spectra concatenated, solid tables merged)."""
 import os
 import subprocess
 import sys
@@ -39,7 +41,8 @@ print("ok")
 
 @pytest.mark.parametrize("var,val", [("MH_SORT_CHUNK_TILES", "1"), ("MH_SORT_CHUNK_TILES", "3"),
                                      ("MH_SPREAD_BITS", "8"), ("MH_SPREAD_BITS", "16"),
-                                     ("MH_SPREAD_BITS", "24")])
+                                     ("MH_SPREAD_BITS", "24"), ("MH_COUNT_BUCKET_BITS", "1"),
+                                     ("MH_COUNT_BUCKET_BITS", "4")])
 def test_small_input_paths_match_oracle(var, val):
     env = dict(os.environ, **{var: val})
     p = subprocess.run([sys.executable, "-c", CHILD], env=env, capture_output=True, text=True, timeout=600)

@@ -243,3 +243,23 @@ def test_mismatched_k_is_einval(mh, ctx):
     with pytest.raises(mh.MhError) as e:
         mh.mh_build_sdbg(ctx, a, b)
     assert e.value.code == mh.MH_EINVAL
+
+
+def test_count_under_hbm_budget_matches_in_memory_count():
+    """A budget too small for the whole key set makes counting go bucket by
+    bucket; the tables must not change."""
+    import paper_1409_7208_gb300 as mh
+    ascii, offs = synth.uniform_genome_reads(1)
+    free = mh.Context(device=0)
+    want = mh.mh_count_kmers(free, mh.mh_pack_reads(free, ascii, offs), 21, 2)
+    ctx = mh.Context(device=0, hbm_budget=40 << 20)
+    reads = mh.mh_pack_reads(ctx, ascii, offs)
+    got = mh.mh_count_kmers(ctx, reads, 21, 2)
+    used, peak = ctx.memory()
+    g, w = got.numpy(), want.numpy()
+    assert np.array_equal(g["keys"], w["keys"]) and np.array_equal(g["counts"], w["counts"])
+    assert g["n_distinct"] == w["n_distinct"] and peak <= 40 << 20
+    # the bucketed spectrum serves the mercy step like the in-memory one
+    m = mh.mh_mercy_kmers(free, reads, got).numpy()
+    w_m = mh.mh_mercy_kmers(free, mh.mh_pack_reads(free, ascii, offs), want).numpy()
+    assert np.array_equal(m["keys"], w_m["keys"]) and np.array_equal(m["counts"], w_m["counts"])
