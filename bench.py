@@ -49,6 +49,15 @@ WORKLOADS = {
         "gen": lambda seed, pairs=10_000_000: __import__("synth").metagenome_reads(seed=seed, n_pairs=pairs),
         "sample": lambda seed, n: __import__("synth").metagenome_reads(seed=seed, n_pairs=n // 2),
     },
+    "outofcore": {
+        "name": "out-of-core: the simulated metagenome at 100M pairs 2x150 bp (200M reads, 30 Gbp) held in "
+                "pinned host memory, streamed to the device every step; keys counted in buckets of their "
+                "top bits under the device-memory plan, k=31, d=2, mercy on",
+        "k": 31, "d": 2, "seed": 4, "host_input": True, "pairs": 100_000_000, "pool": True,
+        "gen": lambda seed, pairs=100_000_000, out=None: __import__("synth").metagenome_reads(
+            seed=seed, n_pairs=pairs, out=out),
+        "sample": lambda seed, n: __import__("synth").metagenome_reads(seed=seed, n_pairs=n // 2),
+    },
     "plain": {
         "name": "plain single job: uniform 50 kbp genome, 10,000 x 100 bp single-end reads, 1% errors, "
                 "k=21, d=2, mercy on",
@@ -68,6 +77,8 @@ def _args():
     p.add_argument("--workload", default="metagenome", choices=sorted(WORKLOADS) + ["multik", "served"])
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--torch-alloc", action="store_true",
+                   help="library buffers from torch's caching allocator in every workload")
     p.add_argument("--pairs", type=int, default=None,
                    help="read pairs (default: 10M for metagenome, 20M for multik; smaller values: "
                         "profiling and test cases only)")
@@ -506,15 +517,30 @@ def main():
             dist.barrier()
 
     k, d = wl["k"], wl["d"]
-    ascii, offs = wl["gen"](wl["seed"] + 1000 * rank, args.pairs or 10_000_000)
+    host_input = wl.get("host_input", False)
+    pairs = args.pairs or wl.get("pairs", 10_000_000)
+    if host_input:
+        # the reads live in pinned host memory and stream to the device in
+        # every step (the library's staged upload overlaps the packing)
+        pin_ascii = torch.empty(2 * pairs * 150, dtype=torch.uint8, pin_memory=True)
+        ascii, offs = wl["gen"](wl["seed"] + 1000 * rank, pairs, out=pin_ascii.numpy())
+        pin_offs = torch.from_numpy(offs.view(np.int64)).pin_memory()
+    else:
+        ascii, offs = wl["gen"](wl["seed"] + 1000 * rank, pairs)
     n_bases = len(ascii)
     # one stream for torch and the library: the launching stream of every
     # kernel, on which every timing event is recorded
     stream = torch.cuda.Stream(device=local)
     torch.cuda.set_stream(stream)
-    ctx = mh.Context(device=local, stream=stream)
-    d_ascii = torch.from_numpy(ascii).cuda()
-    d_offs = torch.from_numpy(offs.view(np.int64)).cuda()
+    # "pool": the library's own stream-ordered pool instead of torch's
+    # caching allocator (at 180 GB of live buffers the caching allocator
+    # falls back to freeing its cache in the middle of a step)
+    ctx = mh.Context(device=local, stream=stream, torch_allocator=not (wl.get("pool") and not args.torch_alloc))
+    if host_input:
+        d_ascii, d_offs = pin_ascii, pin_offs
+    else:
+        d_ascii = torch.from_numpy(ascii).cuda()
+        d_offs = torch.from_numpy(offs.view(np.int64)).cuda()
     torch.cuda.synchronize()
 
     info = {}
@@ -568,6 +594,8 @@ def main():
     clk = clocks.stop()
     ms = t_start.elapsed_time(t_end)
     prof = ctx.profile()
+    info["buckets"] = prof.get("extract_bucket", (0, 0, 0))[0] // args.steps or 1
+    info["peak_GB"] = round(ctx.memory()[1] / 1e9, 1)
     tot = job_totals(dist, "cuda", info["n_kmers"], info["m"], ms)
     ms = tot["ms"]
     n_kmers = info["n_kmers"]
@@ -576,8 +604,9 @@ def main():
                 for i, name in enumerate(["pack", "count", "mercy", "build"])}
 
     # end to end through host buffers: upload of the reads and download of the SdBG
-    pin_ascii = torch.from_numpy(ascii).pin_memory()
-    pin_offs = torch.from_numpy(offs.view(np.int64)).pin_memory()
+    if not host_input:
+        pin_ascii = torch.from_numpy(ascii).pin_memory()
+        pin_offs = torch.from_numpy(offs.view(np.int64)).pin_memory()
     d2h = {"bytes": 0}
     host_bufs = {}
 
@@ -649,11 +678,14 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": wl["name"], "reads": len(offs) - 1, "bases": n_bases, "k": k, "d": d,
                        "per_rank": "independent read set per rank (seed + 1000 * rank)",
+                       "input": "pinned host memory, uploaded inside every step" if host_input
+                                else "device memory (HBM)",
+                       "count_buckets": info.get("buckets"), "peak_device_GB": info.get("peak_GB"),
                        "l2": "inputs larger than L2 (%.1f GB of reads, %.1f GB of keys per step)"
                              % (n_bases / 1e9, info["n_kmers"] * 4 / 1e9)},
             "sdbg_edges_per_s": tot["edges"] * args.steps / (ms / 1e3),
             "phases_ms": phase_ms,
-            "sizes": {key: int(v) for key, v in info.items()},
+            "sizes": {key: int(v) for key, v in info.items() if key not in ("buckets", "peak_GB")},
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clk,
         }

@@ -182,6 +182,9 @@ int mh_create(const mh_config* cfg, mh_ctx** out) {
         ctx->device = cfg->device;
         MH_CUDA(cudaSetDevice(cfg->device));
         MH_CUDA(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, cfg->device));
+        size_t mem_free = 0, mem_total = 0;
+        MH_CUDA(cudaMemGetInfo(&mem_free, &mem_total));
+        ctx->device_bytes = mem_total;
         if (cfg->stream) {
             ctx->stream = (cudaStream_t)cfg->stream;
         } else {
@@ -233,6 +236,7 @@ void mh_destroy(mh_ctx* ctx) {
     cudaFree(ctx->d_status);
     cudaFreeHost(ctx->h_pinned);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -250,13 +254,7 @@ int mh_pack_reads(mh_ctx* ctx, const uint8_t* ascii, uint64_t n_bases, const uin
         } else {
             // monotonicity is checked on the device with the other offset checks
             if (offs[0] != 0 || offs[n_reads] != n_bases) fail(MH_EINVAL, "offs must run from 0 to n_bases");
-            Buf<uint8_t> da(ctx, n_bases + 16);
-            Buf<uint64_t> doff(ctx, n_reads + 1);
-            if (n_bases)
-                MH_CUDA(cudaMemcpyAsync(da.p, ascii, n_bases, cudaMemcpyHostToDevice, ctx->stream));
-            MH_CUDA(cudaMemcpyAsync(doff.p, offs, sizeof(uint64_t) * (n_reads + 1), cudaMemcpyHostToDevice,
-                                    ctx->stream));
-            pack_reads(ctx, da.p, n_bases, doff.p, n_reads, r.get());
+            pack_reads_host(ctx, ascii, n_bases, offs, n_reads, r.get());
         }
         *out = r.release();
     });

@@ -63,15 +63,20 @@ __device__ __forceinline__ uint32_t key_bucket(const Key<NW>& m, int bb) {
 }
 
 // Bucketed extraction: fragments in tasks of kTaskFrags, a warp per task.
-// A first pass counts the windows of every (bucket, task); after a scan of
-// each bucket's row, a bucket's pass writes its keys at exact offsets, in
-// task order, without atomics.
+// A first pass computes every window's bucket (one byte a window, at its
+// window index) and counts the windows of every (bucket, task).  After a
+// scan of each bucket's row, a bucket's pass reads the bytes, queues the
+// positions of its own windows in shared memory and computes keys for full
+// warps of them only, writing them at exact offsets, in task order, without
+// atomics.
 constexpr int kTaskFrags = 64;
 
 template <int NW>
 __global__ void __launch_bounds__(256) task_hist_kernel(const uint32_t* __restrict__ packed,
-                                                        const uint64_t* __restrict__ frag_offs, uint64_t n_frags,
-                                                        int k, int bb, uint64_t n_tasks, uint32_t* __restrict__ cnt) {
+                                                        const uint64_t* __restrict__ frag_offs,
+                                                        const uint64_t* __restrict__ woff, uint64_t n_frags, int k,
+                                                        int bb, uint64_t n_tasks, uint8_t* __restrict__ ids,
+                                                        uint32_t* __restrict__ cnt) {
     __shared__ uint32_t h[8][64];  // per warp, up to 64 buckets
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
@@ -82,12 +87,14 @@ __global__ void __launch_bounds__(256) task_hist_kernel(const uint32_t* __restri
         __syncwarp();
         const uint64_t f1 = (t + 1) * kTaskFrags < n_frags ? (t + 1) * kTaskFrags : n_frags;
         for (uint64_t f = t * kTaskFrags; f < f1; f++) {
-            const uint64_t b = frag_offs[f], L = frag_offs[f + 1] - b;
+            const uint64_t b = frag_offs[f], L = frag_offs[f + 1] - b, w0 = woff[f];
             const uint64_t nwin = L > (uint64_t)k ? L - k : 0;
             for (uint64_t i = lane; i < nwin; i += 32) {
                 const Key<NW> x = load_window<NW>(packed, b + i, K1);
                 const Key<NW> r = key_rc<NW>(x, K1);
-                atomicAdd(&h[wib][key_bucket<NW>(mix_key<NW>(key_less<NW>(r, x) ? r : x), bb)], 1u);
+                const uint32_t bk = key_bucket<NW>(mix_key<NW>(key_less<NW>(r, x) ? r : x), bb);
+                ids[w0 + i] = (uint8_t)bk;
+                atomicAdd(&h[wib][bk], 1u);
             }
         }
         __syncwarp();
@@ -96,38 +103,110 @@ __global__ void __launch_bounds__(256) task_hist_kernel(const uint32_t* __restri
     }
 }
 
-// The mixed canonical keys of bucket `bk`, task t's at off[t] onwards.
+// The mixed canonical keys of bucket `bk`, task t's at off[t] onwards.  A
+// warp reads its task's bucket bytes 16 a lane (the task's windows are
+// contiguous), queues the window numbers of its bucket in shared memory and
+// computes keys 32 at a time: each lane finds its window's fragment by a
+// binary search over the task's fragment table, held in two registers a
+// lane and read by shuffles.
+constexpr int kQueue = 512 + 32;
+
 template <int NW>
 __global__ void __launch_bounds__(256) extract_bucket_kernel(const uint32_t* __restrict__ packed,
                                                              const uint64_t* __restrict__ frag_offs,
-                                                             uint64_t n_frags, int k, int bb, uint32_t bk,
-                                                             uint64_t n_tasks, const uint64_t* __restrict__ off,
+                                                             const uint64_t* __restrict__ woff,
+                                                             const uint8_t* __restrict__ ids, uint64_t n_frags, int k,
+                                                             uint32_t bk, uint64_t n_tasks,
+                                                             const uint64_t* __restrict__ off,
                                                              uint64_t* __restrict__ out) {
-    const int lane = threadIdx.x & 31;
+    __shared__ uint64_t q[8][kQueue];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint64_t* qw = q[wib];
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const int K1 = k + 1;
+    const uint32_t bk4 = bk * 0x01010101u;
     for (uint64_t t = warp; t < n_tasks; t += n_warps) {
-        uint64_t at = off[t];
-        const uint64_t f1 = (t + 1) * kTaskFrags < n_frags ? (t + 1) * kTaskFrags : n_frags;
-        for (uint64_t f = t * kTaskFrags; f < f1; f++) {
-            const uint64_t b = frag_offs[f], L = frag_offs[f + 1] - b;
-            const uint64_t nwin = L > (uint64_t)k ? L - k : 0;
-            for (uint64_t base = 0; base < nwin; base += 32) {
-                const uint64_t i = base + lane;
-                Key<NW> c;
-                bool keep = false;
-                if (i < nwin) {
-                    const Key<NW> x = load_window<NW>(packed, b + i, K1);
-                    const Key<NW> r = key_rc<NW>(x, K1);
-                    c = mix_key<NW>(key_less<NW>(r, x) ? r : x);
-                    keep = key_bucket<NW>(c, bb) == bk;
-                }
-                const uint32_t m = __ballot_sync(0xFFFFFFFFu, keep);
-                if (keep) store_key<NW>(out, at + __popc(m & ((1u << lane) - 1u)), c);
-                at += __popc(m);
+        const uint64_t f0 = t * kTaskFrags;
+        const int nf = (int)((f0 + kTaskFrags < n_frags ? f0 + kTaskFrags : n_frags) - f0);
+        // fragment j of the task: window offset and base, lane j % 32, register j / 32
+        const uint64_t wA = lane < nf ? woff[f0 + lane] : ~0ull;
+        const uint64_t wB = 32 + lane < nf ? woff[f0 + 32 + lane] : ~0ull;
+        const uint64_t bA = lane < nf ? frag_offs[f0 + lane] : 0;
+        const uint64_t bB = 32 + lane < nf ? frag_offs[f0 + 32 + lane] : 0;
+        auto pick = [&](uint64_t ra, uint64_t rb, int j) {
+            const uint64_t x = __shfl_sync(0xFFFFFFFFu, ra, j & 31);
+            const uint64_t y = __shfl_sync(0xFFFFFFFFu, rb, j & 31);
+            return j < 32 ? x : y;
+        };
+        const uint64_t W0 = woff[f0], W1 = woff[f0 + nf];
+        // position in the packed stream of task window w (every lane at once)
+        auto position = [&](uint64_t w) {
+            int lo = 0;
+            for (int step = 32; step; step >>= 1) {
+                const int c = lo + step;
+                const uint64_t wc = pick(wA, wB, c < nf ? c : nf - 1);
+                if (c < nf && wc <= w) lo = c;
             }
+            return pick(bA, bB, lo) + (w - pick(wA, wB, lo));
+        };
+        auto key_at = [&](uint64_t p) {
+            const Key<NW> x = load_window<NW>(packed, p, K1);
+            const Key<NW> r = key_rc<NW>(x, K1);
+            return mix_key<NW>(key_less<NW>(r, x) ? r : x);
+        };
+        uint64_t at = off[t];
+        int qn = 0;
+        for (uint64_t g = W0 / 16; g * 16 < W1; g += 32) {
+            const uint64_t gl = g + lane, w = gl * 16;
+            uint32_t mask = 0;
+            if (w < W1) {
+                const uint4 v = *reinterpret_cast<const uint4*>(ids + w);
+                const uint32_t e[4] = {v.x ^ bk4, v.y ^ bk4, v.z ^ bk4, v.w ^ bk4};
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    // zero bytes of e[j]: windows of bucket bk
+                    const uint32_t z = __vcmpeq4(e[j], 0u);
+                    mask |= ((z & 1u) | ((z >> 7) & 2u) | ((z >> 14) & 4u) | ((z >> 21) & 8u)) << (4 * j);
+                }
+                const uint64_t lo = W0 > w ? W0 - w : 0, hi = W1 - w < 16 ? W1 - w : 16;
+                mask &= (hi >= 16 ? 0xFFFFu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+            }
+            const int c = __popc(mask);
+            int incl = c;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+                if (lane >= d) incl += y;
+            }
+            const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            int o = qn + incl - c;
+            while (mask) {
+                const int j = __ffs(mask) - 1;
+                mask &= mask - 1;
+                qw[o++] = w + j;
+            }
+            qn += total;
+            __syncwarp();
+            int h = 0;
+            for (; qn - h >= 32; h += 32) {
+                const uint64_t p = position(qw[h + lane]);
+                store_key<NW>(out, at + lane, key_at(p));
+                at += 32;
+            }
+            if (h) {
+                const int rem = qn - h;
+                const uint64_t v = lane < rem ? qw[h + lane] : 0;
+                __syncwarp();
+                if (lane < rem) qw[lane] = v;
+                qn = rem;
+            }
+            __syncwarp();
         }
+        // the last, partial warp of positions
+        const uint64_t p = position(lane < qn ? qw[lane] : W0);
+        if (lane < qn) store_key<NW>(out, at + lane, key_at(p));
+        __syncwarp();
     }
 }
 
@@ -536,8 +615,10 @@ template void expand_runs<4>(mh_ctx*, const uint64_t*, uint64_t, int, int, Buf<u
 
 // Buckets of the mixed canonical keys to count one at a time (0 = all at
 // once): with an HBM budget, enough that one bucket's working set (keys,
-// sort buffer, run slots: about 24 nw + 12 bytes a window) takes at most 60%
-// of the budget still free (up to 64 buckets).  MH_COUNT_BUCKET_BITS (0..6)
+// sort buffer, run slots: about 24 nw + 12 bytes a window), with the byte a
+// window of bucket numbers, takes at most 60%
+// of the budget still free (up to 64 buckets); without a budget, of 85% of
+// the device's memory.  MH_COUNT_BUCKET_BITS (0..6)
 // forces it (tests).
 static int count_bucket_bits(mh_ctx* ctx, uint64_t n, int nw) {
     static const int forced = [] {
@@ -546,11 +627,14 @@ static int count_bucket_bits(mh_ctx* ctx, uint64_t n, int nw) {
         return v >= 0 && v <= 6 ? v : -1;
     }();
     if (forced >= 0) return forced;
-    if (!ctx->budget || !n) return 0;
+    if (!n) return 0;
     const double per = 24.0 * nw + 12.0;
-    const double avail = ctx->budget > ctx->in_use ? (double)(ctx->budget - ctx->in_use) : 0.0;
+    const uint64_t budget = ctx->budget ? ctx->budget : ctx->device_bytes / 20 * 17;
+    const double avail = budget > ctx->in_use ? (double)(budget - ctx->in_use) : 0.0;
+    // bucketed, one byte a window (its bucket) stays for the whole count
+    auto need = [&](int bb) { return (bb ? (double)n : 0.0) + (double)n / (double)(1ull << bb) * 1.05 * per; };
     int bb = 0;
-    while (bb < 6 && (double)n / (double)(1ull << bb) * 1.05 * per > 0.6 * avail) bb++;
+    while (bb < 6 && need(bb) > 0.6 * avail) bb++;
     return bb;
 }
 
@@ -612,13 +696,14 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
     // top bits) and counted alone.  The spectrum is the buckets' spectra in
     // bucket order; the solid tables (both strands, real key order) of the
     // buckets are merged.
-    woff.reset();
     const uint32_t nb = 1u << bb;
     const uint64_t n_tasks = ceil_div(F ? F : 1, (uint64_t)kTaskFrags);
     Buf<uint32_t> tcnt(ctx, nb * n_tasks);
+    Buf<uint8_t> ids(ctx, n + 16);  // read 16 at a time
     if (F)
-        MH_LAUNCH(ctx, "bucket_hist", grid_for(ctx, n_tasks * 32, 256, 8), 256, 0, task_hist_kernel<NW>,
-                  reads->packed, reads->frag_offs, F, k, bb, n_tasks, tcnt.p);
+        MH_LAUNCH_B(ctx, "bucket_hist", reads->n_packed / 4 + n, grid_for(ctx, n_tasks * 32, 256, 8), 256, 0,
+                    task_hist_kernel<NW>, reads->packed, reads->frag_offs, woff.p, F, k, bb, n_tasks, ids.p,
+                    tcnt.p);
     else
         tcnt.zero();
     std::vector<uint64_t> hist(nb, 0);
@@ -637,8 +722,8 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
         const uint64_t m = hist[b];
         Buf<uint64_t> keys(ctx, (m ? m : 1) * NW), alt(ctx, (m ? m : 1) * NW);
         if (m)
-            MH_LAUNCH_B(ctx, "extract_bucket", reads->n_packed / 4 + m * 8 * NW, grid_for(ctx, n_tasks * 32, 256, 8),
-                        256, 0, extract_bucket_kernel<NW>, reads->packed, reads->frag_offs, F, k, bb, b, n_tasks,
+            MH_LAUNCH_B(ctx, "extract_bucket", n + m * 8 * NW, grid_for(ctx, n_tasks * 32, 256, 8), 256, 0,
+                        extract_bucket_kernel<NW>, reads->packed, reads->frag_offs, woff.p, ids.p, F, k, b, n_tasks,
                         toff[b].p, keys.p);
         toff[b].reset();
         const bool in_alt = radix_sort_spread<NW>(ctx, keys.p, alt.p, m, bb);
@@ -662,6 +747,8 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
         part_sc.push_back(std::move(sc));
         part_S.push_back(S);
     }
+    ids.reset();
+    woff.reset();
     // spectrum: the buckets' spectra back to back
     uint64_t n_spec = 0, S_tot = 0;
     for (uint32_t b = 0; b < nb; b++) {

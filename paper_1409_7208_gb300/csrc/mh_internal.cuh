@@ -50,6 +50,8 @@ struct mh_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t copy_stream = nullptr;  // host uploads overlapped with packing (created on first use)
+    uint64_t device_bytes = 0;           // the device's memory, for plans when no budget is set
     mh_alloc_fn alloc = nullptr;
     mh_free_fn free_fn = nullptr;
     void* alloc_user = nullptr;
@@ -610,6 +612,10 @@ void set_differences(mh_ctx* ctx, const uint64_t* X, uint64_t nx, const uint64_t
 template <int NW>
 void walk_contigs(mh_ctx* ctx, const mh_kmers* solid, const mh_kmers* mercy, uint64_t n_walks, uint32_t max_len,
                   uint64_t seed, mh_contigs* out);
+void pack_reads(mh_ctx* ctx, const uint8_t* d_ascii, uint64_t n_bases, const uint64_t* d_offs, uint64_t n_reads,
+                mh_reads* out);
+void pack_reads_host(mh_ctx* ctx, const uint8_t* h_ascii, uint64_t n_bases, const uint64_t* h_offs, uint64_t n_reads,
+                     mh_reads* out);
 void pack_with_contigs(mh_ctx* ctx, const uint8_t* d_ascii, uint64_t n_bases, const uint64_t* d_offs,
                        uint64_t n_reads, const mh_contigs* contigs, uint32_t copies, mh_reads* out);
 

@@ -6,6 +6,8 @@
 // the reads and the packed words are the output.  Otherwise the valid bases
 // are compacted (scan of per-chunk valid counts) and fragment starts are
 // found from the validity masks and the read starts.
+#include <cstdlib>
+
 #include "mh_internal.cuh"
 
 namespace mh {
@@ -257,6 +259,95 @@ void pack_reads(mh_ctx* ctx, const uint8_t* d_ascii, uint64_t n_bases, const uin
     out->packed = cp.release();
     out->frag_offs = fo.release();
     out->frag_read = fr.release();
+}
+
+// Reads in host memory (pinned for overlap): the ASCII streams through two
+// device staging buffers of kPiece bytes on the context's copy stream while
+// the context stream packs the piece before (piece starts are multiples of
+// 16 bases, so every piece fills whole packed words of its own).  Only the
+// packed stream and the offsets stay on the device.  If some byte is not a
+// base or some read is empty, the fragments must be found and the bases
+// compacted: the ASCII is then uploaded whole and packed as from the device.
+constexpr uint64_t kPiece = 256ull << 20;
+
+// staging piece in bytes: kPiece, or MH_PACK_PIECE (a multiple of 16; tests)
+static uint64_t piece_bytes() {
+    static const uint64_t v = [] {
+        const char* e = std::getenv("MH_PACK_PIECE");
+        const long long x = e ? std::atoll(e) : 0;
+        return x >= 16 ? (uint64_t)x / 16 * 16 : kPiece;
+    }();
+    return v;
+}
+
+static cudaStream_t copy_stream(mh_ctx* ctx) {
+    if (!ctx->copy_stream) MH_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    return ctx->copy_stream;
+}
+
+void pack_reads_host(mh_ctx* ctx, const uint8_t* h_ascii, uint64_t n_bases, const uint64_t* h_offs, uint64_t n_reads,
+                     mh_reads* out) {
+    cudaStream_t cs = copy_stream(ctx);
+    const uint64_t n_chunks = ceil_div(n_bases, 16);
+    const uint64_t piece = n_bases < piece_bytes() ? ceil_div(n_bases ? n_bases : 1, 16) * 16 : piece_bytes();
+    const uint64_t n_pieces = ceil_div(n_bases, piece);
+    Buf<uint64_t> doff(ctx, n_reads + 1);
+    Buf<uint32_t> flags(ctx, 2);  // [0] any invalid byte, [1] any empty read
+    flags.zero();
+    Buf<uint32_t> packed(ctx, n_chunks + kPackPad);
+    MH_CUDA(cudaMemsetAsync(packed.p + n_chunks, 0, kPackPad * sizeof(uint32_t), ctx->stream));
+    Buf<uint8_t> stage[2] = {Buf<uint8_t>(ctx, n_pieces ? piece : 1), Buf<uint8_t>(ctx, n_pieces > 1 ? piece : 1)};
+    cudaEvent_t ev[5] = {};
+    auto done = [&] {
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
+    };
+    try {
+        for (auto& e : ev) MH_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        // the copy stream writes buffers just allocated on the context stream
+        MH_CUDA(cudaEventRecord(ev[4], ctx->stream));
+        MH_CUDA(cudaStreamWaitEvent(cs, ev[4], 0));
+        MH_CUDA(cudaMemcpyAsync(doff.p, h_offs, sizeof(uint64_t) * (n_reads + 1), cudaMemcpyHostToDevice, cs));
+        MH_CUDA(cudaEventRecord(ev[4], cs));
+        MH_CUDA(cudaStreamWaitEvent(ctx->stream, ev[4], 0));
+        MH_LAUNCH(ctx, "check_offs", grid_for(ctx, n_reads, 256), 256, 0, check_offs_kernel, doff.p, n_reads,
+                  n_bases, flags.p + 1, ctx->d_status);
+        for (uint64_t q = 0; q < n_pieces; q++) {
+            const int s = (int)(q & 1);
+            const uint64_t b = q * piece, len = n_bases - b < piece ? n_bases - b : piece;
+            if (q >= 2) MH_CUDA(cudaStreamWaitEvent(cs, ev[2 + s], 0));  // piece q-2 packed
+            MH_CUDA(cudaMemcpyAsync(stage[s].p, h_ascii + b, len, cudaMemcpyHostToDevice, cs));
+            MH_CUDA(cudaEventRecord(ev[s], cs));
+            MH_CUDA(cudaStreamWaitEvent(ctx->stream, ev[s], 0));
+            MH_LAUNCH(ctx, "pack_chunks", grid_for(ctx, ceil_div(len, 16), 256), 256, 0, pack_chunks_kernel,
+                      stage[s].p, len, true, packed.p + b / 16, flags.p);
+            MH_CUDA(cudaEventRecord(ev[2 + s], ctx->stream));
+        }
+    } catch (...) {
+        done();
+        throw;
+    }
+    done();
+    stage[0].reset();
+    stage[1].reset();
+    uint64_t fl[1];
+    read_u64(ctx, reinterpret_cast<const uint64_t*>(flags.p), fl, 1);
+    if ((fl[0] & 0xFFFFFFFFull) == 0 && (fl[0] >> 32) == 0) {
+        Buf<uint32_t> fr(ctx, n_reads);
+        if (n_reads) MH_LAUNCH(ctx, "iota", grid_for(ctx, n_reads, 256), 256, 0, iota_u32_kernel, fr.p, n_reads);
+        out->n_reads = n_reads;
+        out->n_bases = n_bases;
+        out->n_frags = n_reads;
+        out->n_packed = n_bases;
+        out->packed = packed.release();
+        out->frag_offs = doff.release();
+        out->frag_read = fr.release();
+        return;
+    }
+    packed.reset();
+    Buf<uint8_t> da(ctx, n_bases + 16);
+    if (n_bases) MH_CUDA(cudaMemcpyAsync(da.p, h_ascii, n_bases, cudaMemcpyHostToDevice, ctx->stream));
+    pack_reads(ctx, da.p, n_bases, doff.p, n_reads, out);
 }
 
 }  // namespace mh

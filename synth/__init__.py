@@ -76,12 +76,17 @@ def genome_codes(seed: int, lens) -> np.ndarray:
 
 
 def _sample(seed, codes, lens, weight, n_units, read_len, paired, insert_mean, insert_sd,
-            err, err_ramp):
+            err, err_ramp, out=None):
     lib = _load()
     lens = np.ascontiguousarray(lens, dtype=np.uint64)
     weight = np.ascontiguousarray(weight, dtype=np.float64)
     n_reads = n_units * (2 if paired else 1)
-    ascii = np.empty(n_reads * read_len, dtype=np.uint8)
+    if out is None:
+        ascii = np.empty(n_reads * read_len, dtype=np.uint8)
+    else:
+        if out.dtype != np.uint8 or not out.flags.c_contiguous or len(out) < n_reads * read_len:
+            raise ValueError("out must be a contiguous uint8 array of n_reads * read_len bytes")
+        ascii = out[: n_reads * read_len]
     rc = lib.synth_reads(seed, _ptr(codes, ctypes.c_uint8), len(lens), _ptr(lens, ctypes.c_uint64),
                          _ptr(weight, ctypes.c_double), n_units, read_len, 1 if paired else 0,
                          insert_mean, insert_sd, err, 1 if err_ramp else 0,
@@ -120,12 +125,13 @@ def metagenome_genomes(seed: int = 2, n_genomes: int = 100, median_len: float = 
 def metagenome_reads(seed: int = 2, n_genomes: int = 100, median_len: float = 2e6,
                      sigma_len: float = 0.5, sigma_ab: float = 1.5, n_pairs: int = 10_000_000,
                      read_len: int = 150, insert_mean: float = 350.0, insert_sd: float = 35.0,
-                     err_3p: float = 0.01):
+                     err_3p: float = 0.01, out=None):
     """Simulated metagenome: genomes picked with probability proportional to
     abundance x length; paired reads (mate 2 = reverse complement of the
     fragment's end; insert ~ N(350, 35)); substitution rate
     ``err_3p * (i + 0.5) / read_len`` at read position i (mean 0.5% for the
-    default 1% at the 3' end).
+    default 1% at the 3' end).  ``out``: a uint8 buffer to write the reads
+    into (pinned host memory, say); the returned ``ascii`` is a view of it.
 
     The defaults are the full simulated-metagenome workload: 100 genomes,
     median 2 Mbp, 10 M pairs of 2 x 150 bp (3.0 Gbp), seed 2.
@@ -133,7 +139,7 @@ def metagenome_reads(seed: int = 2, n_genomes: int = 100, median_len: float = 2e
     lens, ab, codes = metagenome_genomes(seed, n_genomes, median_len, sigma_len, sigma_ab)
     weight = ab * lens.astype(np.float64)
     return _sample(seed, codes, lens, weight, n_pairs, read_len, True, insert_mean, insert_sd,
-                   err_3p, True)
+                   err_3p, True, out)
 
 
 def random_reads(seed: int, n_reads: int, min_len: int, max_len: int, p_invalid: float = 0.0,

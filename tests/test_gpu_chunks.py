@@ -5,8 +5,10 @@ between chunks; 1 or 3 tiles per chunk), and the count sort's fix-up of
 keys sharing their top bits (passes over the top 8, 16 or 24 bits only, so
 that groups of every size occur: a few keys sorted by one thread, tens to
 thousands by a warp or a CTA, and crowded groups by the segment fallback),
-and the out-of-core count (2 or 16 buckets of keys counted one at a time,
-spectra concatenated, solid tables merged)."""
+the out-of-core count (2 or 16 buckets of keys counted one at a time,
+spectra concatenated, solid tables merged), and reads streamed from host
+memory through staging pieces of 48 bytes or 4 KB (pieces that end inside a
+read, reads that span several pieces, invalid bytes found mid-stream)."""
 import os
 import subprocess
 import sys
@@ -22,6 +24,20 @@ import sys, numpy as np
 sys.path.insert(0, %r)
 import oracle, synth, paper_1409_7208_gb300 as mh
 ctx = mh.Context(device=0)
+shifts = (30 - 2 * np.arange(16)).astype(np.uint32)
+for a, o in (synth.random_reads(5, 400, 0, 300), synth.random_reads(6, 300, 0, 200, p_invalid=0.02),
+             synth.random_reads(7, 50, 0, 40, p_lower=0.3)):
+    bases, fo, fr = oracle.fragments(a, o)
+    r = mh.mh_pack_reads(ctx, a, o).tensors()
+    codes = np.zeros((len(bases) + 15) // 16 * 16, dtype=np.uint32)
+    codes[: len(bases)] = np.frombuffer(bases, dtype=np.uint8) if isinstance(bases, bytes) else bases
+    lut = np.zeros(256, dtype=np.uint32)
+    lut[list(b"ACGT")] = np.arange(4, dtype=np.uint32)
+    words = np.bitwise_or.reduce(lut[codes].reshape(-1, 16) << shifts, axis=1).astype(np.uint32)
+    assert r["n_packed"] == len(bases) and r["n_frags"] == len(fr)
+    assert np.array_equal(r["packed"].cpu().numpy().view(np.uint32), words)
+    assert np.array_equal(r["frag_offs"].cpu().numpy().view(np.uint64), fo)
+    assert np.array_equal(r["frag_read"].cpu().numpy().view(np.uint32), fr)
 for seed, k, n_reads in ((1, 21, 3000), (2, 31, 2500), (3, 47, 1500), (4, 99, 900)):
     ascii, offs = synth.uniform_genome_reads(seed, 4000, n_reads, 150, 0.01)
     reads = mh.mh_pack_reads(ctx, ascii, offs)
@@ -42,7 +58,8 @@ print("ok")
 @pytest.mark.parametrize("var,val", [("MH_SORT_CHUNK_TILES", "1"), ("MH_SORT_CHUNK_TILES", "3"),
                                      ("MH_SPREAD_BITS", "8"), ("MH_SPREAD_BITS", "16"),
                                      ("MH_SPREAD_BITS", "24"), ("MH_COUNT_BUCKET_BITS", "1"),
-                                     ("MH_COUNT_BUCKET_BITS", "4")])
+                                     ("MH_COUNT_BUCKET_BITS", "4"), ("MH_PACK_PIECE", "48"),
+                                     ("MH_PACK_PIECE", "4096")])
 def test_small_input_paths_match_oracle(var, val):
     env = dict(os.environ, **{var: val})
     p = subprocess.run([sys.executable, "-c", CHILD], env=env, capture_output=True, text=True, timeout=600)
