@@ -74,9 +74,11 @@ def _args():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="metagenome", choices=sorted(WORKLOADS) + ["multik", "served"])
+    p.add_argument("--workload", default="metagenome",
+                   choices=sorted(WORKLOADS) + ["multik", "served", "batched"])
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workers", type=int, default=None, help="worker streams of the batched workload (4)")
     p.add_argument("--torch-alloc", action="store_true",
                    help="library buffers from torch's caching allocator in every workload")
     p.add_argument("--pairs", type=int, default=None,
@@ -336,6 +338,160 @@ def run_multik(args, rank, world, local):
         dist.destroy_process_group()
 
 
+BATCHED = {
+    "name": "batched: 64 independent read sets, reads per set lognormal (ln-median halfway between 50k and 5M, "
+            "sigma a quarter of that span) clipped to [50k, 5M], pairs of 2x150 bp, each set a 10-genome "
+            "mini-metagenome (genomes lognormal, median 2 Mbp), 3' error ramp to 1% (mean 0.5%), k=31, d=2, "
+            "mercy on; the whole batch through mh_run_batch on 4 worker streams, tile shape autotuned",
+    "n_sets": 64, "k": 31, "d": 2, "seed": 5, "workers": 4,
+}
+
+
+def run_batched(args, rank, world, local):
+    """One step = the whole path on all 64 read sets through mh_run_batch
+    (worker streams, largest set first); value = (k+1)-mers of all sets per
+    second.  The same sets through the plain calls one after another on one
+    stream are timed beside it (serial_value)."""
+    import numpy as np
+    import torch
+
+    import paper_1409_7208_gb300 as mh
+    import synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sets = synth.batch_sets(BATCHED["seed"] + 1000 * rank, BATCHED["n_sets"])
+    n_reads = sum(len(o) - 1 for _, o in sets)
+    n_bases = sum(len(a) for a, _ in sets)
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
+    ctx = mh.Context(device=local, stream=stream, torch_allocator=False)
+    dev = [(torch.from_numpy(a).cuda(), torch.from_numpy(o.view(np.int64)).cuda()) for a, o in sets]
+    torch.cuda.synchronize()
+    k, d, W = BATCHED["k"], BATCHED["d"], args.workers or BATCHED["workers"]
+    info = {}
+
+    def batched(inputs, download=None):
+        res = mh.mh_run_batch(ctx, inputs, k, d, workers=W, autotune=True)
+        info["n_kmers"] = sum(r["solid"].view().n_kmers for r in res)
+        info["m"] = sum(r["sdbg"].view().m for r in res)
+        if download is not None:
+            for r in res:
+                download(r["sdbg"])
+        for r in res:
+            for key in ("sdbg", "mercy", "solid"):
+                r[key].free()
+
+    def serial(inputs):
+        for a, o in inputs:
+            reads = mh.mh_pack_reads(ctx, a, o)
+            solid = mh.mh_count_kmers(ctx, reads, k, d)
+            mercy = mh.mh_mercy_kmers(ctx, reads, solid)
+            g = mh.mh_build_sdbg(ctx, solid, mercy)
+            del g, mercy, solid, reads
+
+    def timed(fn, n):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(n):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / n
+
+    for _ in range(args.warmup):
+        batched(dev)
+    if dist is not None:
+        dist.barrier()
+    # the plain path, one set after another (kernels alone: the roofline)
+    serial(dev)
+    ctx.profile_reset()
+    ctx.set_profile(True)
+    serial_ms = timed(lambda: serial(dev), 1)
+    ctx.set_profile(False)
+    prof_serial = ctx.profile()
+    clocks = Clocks(local)
+    clocks.start()
+    ctx.profile_reset()
+    ctx.set_profile(True)
+    ms = timed(lambda: batched(dev), args.steps)
+    ctx.set_profile(False)
+    clk = clocks.stop()
+    prof = ctx.profile()
+    tot = job_totals(dist, "cuda", info["n_kmers"], info["m"], ms)
+    ms = tot["ms"]
+    value = tot["kmers"] / (ms / 1e3)
+
+    e2e = None
+    if args.e2e_steps > 0:
+        pinned = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(o.view(np.int64)).pin_memory())
+                  for a, o in sets]
+        nbytes = {"d2h": 0}
+
+        def download(g):
+            t = g.tensors()
+            with torch.cuda.stream(stream):
+                for key in ("W", "last", "valid", "dummy", "aux"):
+                    src = t[key]
+                    buf = torch.empty(max(1, src.numel()), dtype=src.dtype, pin_memory=True)
+                    if src.numel():
+                        buf[: src.numel()].view(src.shape).copy_(src, non_blocking=True)
+                    nbytes["d2h"] += src.numel() * src.element_size()
+            stream.synchronize()
+
+        batched(pinned, download)
+        torch.cuda.synchronize()
+        nbytes["d2h"] = 0
+        e0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            batched(pinned, download)
+        torch.cuda.synchronize()
+        e_s = (time.perf_counter() - e0) / args.e2e_steps
+        e2e = {"value": info["n_kmers"] / e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(n_bases + 8 * (n_reads + len(sets))),
+               "d2h_bytes_per_step": int(nbytes["d2h"] / args.e2e_steps + 48 * len(sets))}
+
+    peak, peak_kind = _peak_hbm()
+    launches, o_ms, o_bytes = prof_serial.get("radix_onesweep", (0, 0.0, 0))
+    achieved = o_bytes / (o_ms / 1e3) / 1e9 if o_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": "radix_onesweep", "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "launches": launches,
+                "note": "from the plain serial pass (kernels timed alone); in the batch, kernels of "
+                        "several streams share the GPU and per-launch times overlap"}
+    kernels = {name: {"launches": la, "ms_per_step": t / args.steps}
+               for name, (la, t, b) in sorted(prof.items(), key=lambda kv: -kv[1][1])[:12]}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sa, so = sets[0]
+        ns = min(CPU_SAMPLE_READS, len(so) - 1)
+        sa, so = sa[: int(so[ns])], so[: ns + 1]
+        n_s, t_s = cpu_oracle_run(sa, so, k, d)
+        cpu = {"value": n_s / t_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "first %d reads of set 0 (%d (k+1)-mers on both strands), %.1f s" % (ns, n_s, t_s)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": BATCHED["name"], "sets": len(sets), "reads": n_reads, "bases": n_bases,
+                           "k": k, "d": d, "workers": W, "sort_shape": mh.mh_sort_shape(ctx),
+                           "l2": "inputs larger than L2 (%.1f GB of reads)" % (n_bases / 1e9)},
+                "serial_value": info["n_kmers"] / (serial_ms / 1e3), "serial_ms": serial_ms,
+                "batch_speedup": serial_ms / ms,
+                "sdbg_edges_per_s": tot["edges"] / (ms / 1e3),
+                "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": sum(la for (la, _, _) in prof.values()) // args.steps * args.steps,
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 SERVED = {
     "name": "served: Poisson arrivals (20/s) for 15 s of count+mercy+build jobs; reads per job lognormal "
             "(median 20k, sigma ln(2000)/4) clipped to [2k, 1M] (the served config's distribution scaled by "
@@ -474,6 +630,32 @@ def main():
                                   "the oracle would take hours for its jobs"}), flush=True)
             return
         return run_served(args, rank, local)
+    if args.workload == "batched":
+        if args.impl == "reference":
+            if rank == 0:
+                import synth
+                sa, so = synth.batch_sets(BATCHED["seed"], 1)[0]
+                ns = min(CPU_SAMPLE_READS, len(so) - 1)
+                sa, so = sa[: int(so[ns])], so[: ns + 1]
+                for _ in range(args.warmup):
+                    cpu_oracle_run(sa, so, BATCHED["k"], BATCHED["d"])
+                n_s = t_s = 0
+                for _ in range(args.steps):
+                    n, t = cpu_oracle_run(sa, so, BATCHED["k"], BATCHED["d"])
+                    n_s += n
+                    t_s += t
+                v = n_s / t_s
+                print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+                                  "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                                  "ms_per_step": 1e3 * t_s / args.steps, "higher_is_better": True,
+                                  "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                                  "config": {"workload": BATCHED["name"], "sample_reads": ns},
+                                  "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                                   "sample": "first %d reads of set 0" % ns},
+                                  "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                          "d2h_bytes_per_step": 0}}), flush=True)
+            return
+        return run_batched(args, rank, world, local)
     if args.workload == "multik":
         if args.impl == "reference":
             if rank == 0:

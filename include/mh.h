@@ -233,6 +233,61 @@ void mh_free_contigs(mh_contigs* c);
 int mh_pack_reads_contigs(mh_ctx* ctx, const uint8_t* ascii, uint64_t n_bases, const uint64_t* offs,
                           uint64_t n_reads, const mh_contigs* contigs, int copies, mh_reads** out);
 
+/* ------------------------------------------------------ batched sets */
+
+/* One read set of a batch: reads back to back with n_reads + 1 offsets, as
+ * for mh_pack_reads; on_device = 1 when ascii and offs are device pointers
+ * (they must stay valid and unchanged until mh_run_batch returns). */
+typedef struct {
+    const uint8_t* ascii;
+    uint64_t n_bases;
+    const uint64_t* offs;
+    uint64_t n_reads;
+    int on_device;
+} mh_read_set;
+
+/* The outputs of one set: handles as mh_count_kmers, mh_mercy_kmers and
+ * mh_build_sdbg return them (NULL where the flags skip the step or the set
+ * failed), owned by the caller (mh_free_*, before mh_destroy of the
+ * context), and the set's status (MH_OK or the error of its first failing
+ * step; a failed set keeps no outputs). */
+typedef struct {
+    mh_kmers* solid;
+    mh_kmers* mercy;
+    mh_sdbg* sdbg;
+    int status;
+} mh_set_result;
+
+#define MH_BATCH_MERCY 1     /* run mh_mercy_kmers on each set */
+#define MH_BATCH_BUILD 2     /* run mh_build_sdbg (solid + mercy) on each set */
+#define MH_BATCH_AUTOTUNE 4  /* time the scatter pass's tile shapes once per context and k */
+
+/* Run the whole path (Sec. 2, paragraphs 1-3: pack, count with the solid
+ * filter, mercy, SdBG) on n_sets independent read sets, each an independent
+ * problem, k and d shared.  `workers` (1..64) host threads each drive a
+ * worker context of ctx (its own stream and stream-ordered pool, created on
+ * first use and kept until mh_destroy) and take sets largest first; a set
+ * starts when its estimated working set fits ctx's HBM budget (without one,
+ * 85% of the device's memory) next to the sets in flight, or when none is.
+ * Sets run concurrently on the workers' streams.  Work on ctx's stream before
+ * the call is ordered before every set; ctx's stream waits for every set's
+ * last kernel, so work queued on it after the call sees all outputs.  With
+ * profiling on, the workers' kernel statistics are added to ctx's.
+ * MH_BATCH_AUTOTUNE: before the first batch at a given k of 1-word keys,
+ * counts the largest set once with each tile shape of the scatter pass
+ * (items per thread x resident CTAs per SM) and keeps the fastest for the
+ * context (mh_sort_shape reports it).  Returns MH_OK when every set
+ * succeeded, else the first failing set's error (out[i].status tells which).
+ * Not to be called concurrently on one context.  Errors: MH_EINVAL (NULL
+ * pointers, n_sets < 0, workers outside 1..64, k or d out of range). */
+int mh_run_batch(mh_ctx* ctx, const mh_read_set* sets, int n_sets, int k, int d, int workers, int flags,
+                 mh_set_result* out);
+
+/* The scatter-pass tile shape the context uses for 1-word keys: 0 = 12 keys
+ * a thread at 4 CTAs per SM (the default), 1 = 14 at 3, 2 = 12 at 3; -1
+ * before any autotuning (the default applies). */
+int mh_sort_shape(const mh_ctx* ctx);
+
 /* ------------------------------------------------- no-allocation sort */
 
 /* Sort n keys (nw = 1, 2 or 4 words each, layout as above) ascending by their

@@ -35,8 +35,10 @@ SYMBOLS = (
     "mh_sdbg_view_get", "mh_free_sdbg", "mh_strerror", "mh_last_error_message", "mh_stream",
     "mh_memory", "mh_profile_count", "mh_profile_get", "mh_profile_reset", "mh_set_profile",
     "mh_sort_keys_noalloc", "mh_walk_contigs", "mh_contigs_view_get", "mh_free_contigs",
-    "mh_pack_reads_contigs", "mh_trim",
+    "mh_pack_reads_contigs", "mh_trim", "mh_run_batch", "mh_sort_shape",
 )
+
+MH_BATCH_MERCY, MH_BATCH_BUILD, MH_BATCH_AUTOTUNE = 1, 2, 4
 
 
 class MhError(RuntimeError):
@@ -71,6 +73,16 @@ class SdbgView(ctypes.Structure):
                 ("u", ctypes.c_uint64), ("n_nodes", ctypes.c_uint64), ("F", ctypes.c_uint64 * 6),
                 ("W", ctypes.c_void_p), ("last", ctypes.c_void_p), ("valid", ctypes.c_void_p),
                 ("dummy", ctypes.c_void_p), ("aux", ctypes.c_void_p), ("mult", ctypes.c_void_p)]
+
+
+class ReadSet(ctypes.Structure):
+    _fields_ = [("ascii", ctypes.c_void_p), ("n_bases", ctypes.c_uint64), ("offs", ctypes.c_void_p),
+                ("n_reads", ctypes.c_uint64), ("on_device", ctypes.c_int)]
+
+
+class SetResult(ctypes.Structure):
+    _fields_ = [("solid", ctypes.c_void_p), ("mercy", ctypes.c_void_p), ("sdbg", ctypes.c_void_p),
+                ("status", ctypes.c_int)]
 
 
 class ContigsView(ctypes.Structure):
@@ -122,6 +134,9 @@ def load_library(path: str = LIB_PATH):
     lib.mh_free_contigs.argtypes = [P]
     lib.mh_pack_reads_contigs.argtypes = [P, P, u64, P, u64, P, ctypes.c_int, PP]
     lib.mh_trim.argtypes = [P]
+    lib.mh_run_batch.argtypes = [P, ctypes.POINTER(ReadSet), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_int, ctypes.POINTER(SetResult)]
+    lib.mh_sort_shape.argtypes = [P]
     _lib = lib
     return lib
 
@@ -452,6 +467,51 @@ def mh_walk_contigs(ctx: Context, solid: Kmers, mercy: Kmers | None, n_walks: in
     ctx._check(ctx._lib.mh_walk_contigs(ctx._h, solid._h, mercy._h if mercy is not None else None, int(n_walks),
                                         int(max_len), int(seed), ctypes.byref(h)))
     return Contigs(ctx, h)
+
+
+def mh_run_batch(ctx: Context, sets, k: int, d: int = 2, workers: int = 4, mercy: bool = True,
+                 build: bool = True, autotune: bool = False) -> list:
+    """The whole path on many independent read sets at once (``sets``: a list
+    of (ascii, offs) pairs, each as for :func:`mh_pack_reads`), on
+    ``workers`` concurrent worker streams, largest set first.  Returns one
+    dict per set, in input order: ``solid``, ``mercy``, ``sdbg`` handles
+    (None where skipped).  Raises :class:`MhError` if a set failed (after
+    freeing every output)."""
+    arr = (ReadSet * max(1, len(sets)))()
+    keep = []
+    for i, (ascii, offs) in enumerate(sets):
+        if isinstance(ascii, np.ndarray):
+            ascii = np.ascontiguousarray(ascii, dtype=np.uint8)
+            offs = np.ascontiguousarray(offs, dtype=np.uint64)
+        keep.append((ascii, offs))
+        pa, da = _ptr_of(ascii)
+        po, do = _ptr_of(offs)
+        if da != do:
+            raise ValueError("set %d: ascii and offs must both be on the host or both on the device" % i)
+        n_bases = int(ascii.shape[0])
+        arr[i] = ReadSet(pa if n_bases else None, n_bases, po, int(offs.shape[0]) - 1, da)
+    res = (SetResult * max(1, len(sets)))()
+    flags = (MH_BATCH_MERCY if mercy else 0) | (MH_BATCH_BUILD if build else 0) | \
+        (MH_BATCH_AUTOTUNE if autotune else 0)
+    rc = ctx._lib.mh_run_batch(ctx._h, arr, len(sets), int(k), int(d), int(workers), flags, res)
+    out = []
+    for i in range(len(sets)):
+        r = res[i]
+        out.append({"solid": Kmers(ctx, r.solid) if r.solid else None,
+                    "mercy": Kmers(ctx, r.mercy) if r.mercy else None,
+                    "sdbg": Sdbg(ctx, r.sdbg) if r.sdbg else None, "status": r.status})
+    if rc != MH_OK:
+        for o in out:
+            for key in ("sdbg", "mercy", "solid"):
+                if o[key] is not None:
+                    o[key].free()
+        ctx._check(rc)
+    return out
+
+
+def mh_sort_shape(ctx: Context) -> int:
+    """The scatter tile shape the context uses for 1-word keys (-1: default)."""
+    return int(ctx._lib.mh_sort_shape(ctx._h))
 
 
 def mh_pack_reads_contigs(ctx: Context, ascii, offs, contigs: Contigs | None, copies: int) -> Reads:

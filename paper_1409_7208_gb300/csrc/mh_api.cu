@@ -144,6 +144,30 @@ void sync_and_check(mh_ctx* ctx) {
     }
 }
 
+// Add src's kernel statistics to dst's (by kernel name) and clear src's.
+void profile_merge(mh_ctx* dst, mh_ctx* src) {
+    cudaStreamSynchronize(src->stream);
+    drain_events(src, true);
+    for (size_t i = 0; i < src->names.size(); i++) {
+        KernelStat& s = src->stats[i];
+        if (!s.launches) continue;
+        auto it = dst->name_id.find(src->names[i]);
+        int id;
+        if (it == dst->name_id.end()) {
+            id = (int)dst->names.size();
+            dst->name_id[src->names[i]] = id;
+            dst->names.push_back(src->names[i]);
+            dst->stats.emplace_back();
+        } else {
+            id = it->second;
+        }
+        dst->stats[id].launches += s.launches;
+        dst->stats[id].total_ms += s.total_ms;
+        dst->stats[id].bytes += s.bytes;
+        s = KernelStat();
+    }
+}
+
 void read_u64(mh_ctx* ctx, const uint64_t* d, uint64_t* h, int count) {
     if (count > 62) fail(MH_EINVAL, "read_u64: too many words");
     MH_CUDA(cudaMemcpyAsync(ctx->h_pinned, d, sizeof(uint64_t) * count, cudaMemcpyDeviceToHost, ctx->stream));
@@ -226,6 +250,7 @@ int mh_create(const mh_config* cfg, mh_ctx** out) {
 
 void mh_destroy(mh_ctx* ctx) {
     if (!ctx) return;
+    for (mh_ctx* w : ctx->workers) mh_destroy(w);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     for (auto& p : ctx->pending) {

@@ -51,6 +51,9 @@ struct mh_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t copy_stream = nullptr;  // host uploads overlapped with packing (created on first use)
+    std::vector<mh_ctx*> workers;        // worker contexts of mh_run_batch (created on first use)
+    int sort_shape = -1;                 // scatter tile shape for 1-word keys (-1: default)
+    int tuned_k = -1;                    // k the shape was tuned at
     uint64_t device_bytes = 0;           // the device's memory, for plans when no budget is set
     mh_alloc_fn alloc = nullptr;
     mh_free_fn free_fn = nullptr;

@@ -76,7 +76,8 @@ static bool radix_sort_impl(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t
 // Tile shape of the scatter pass for 1-word keys: (items per thread,
 // resident CTAs per SM).  The defaults, (12, 4) for keys alone and (12, 3)
 // with a payload (which needs more than 64 registers), measured fastest on
-// GB300; MH_SORT_VARIANT selects another key-only shape for tuning runs.
+// GB300; a context's tuned shape (mh_run_batch's autotuner) or
+// MH_SORT_VARIANT selects another key-only shape.
 static int sort_variant() {
     static int v = [] {
         const char* e = std::getenv("MH_SORT_VARIANT");
@@ -92,7 +93,7 @@ static bool radix_sort_dispatch(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint
         if constexpr (HV) {
             return radix_sort_impl<NW, HV, 12, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
         } else {
-            switch (sort_variant()) {
+            switch (ctx->sort_shape >= 0 ? ctx->sort_shape : sort_variant()) {
                 case 1: return radix_sort_impl<NW, HV, 14, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
                 case 2: return radix_sort_impl<NW, HV, 12, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
                 default: return radix_sort_impl<NW, HV, 12, 4>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);

@@ -142,6 +142,28 @@ def metagenome_reads(seed: int = 2, n_genomes: int = 100, median_len: float = 2e
                    err_3p, True, out)
 
 
+def batch_read_counts(seed: int = 5, n_sets: int = 64, lo: int = 50_000, hi: int = 5_000_000) -> np.ndarray:
+    """Read counts of a batch: lognormal with ln-median halfway between ln lo
+    and ln hi and sigma a quarter of that span, clipped to [lo, hi], rounded
+    down to an even count (pairs)."""
+    rng = np.random.default_rng(seed)
+    mu = (np.log(lo) + np.log(hi)) / 2
+    sigma = (np.log(hi) - np.log(lo)) / 4
+    n = np.clip(np.exp(rng.normal(mu, sigma, size=n_sets)), lo, hi).astype(np.int64)
+    return n // 2 * 2
+
+
+def batch_sets(seed: int = 5, n_sets: int = 64, lo: int = 50_000, hi: int = 5_000_000,
+               read_len: int = 150, err_3p: float = 0.01):
+    """Independent read sets of a batch: set i is a 10-genome mini-metagenome
+    (``metagenome_reads`` with 10 genomes, seed ``seed * 1000 + i``) of
+    ``batch_read_counts`` reads in pairs of ``read_len`` bp, substitution rate
+    rising to ``err_3p`` at the 3' end (mean 0.5%)."""
+    counts = batch_read_counts(seed, n_sets, lo, hi)
+    return [metagenome_reads(seed=seed * 1000 + i, n_genomes=10, n_pairs=int(c) // 2, read_len=read_len,
+                             err_3p=err_3p) for i, c in enumerate(counts)]
+
+
 def random_reads(seed: int, n_reads: int, min_len: int, max_len: int, p_invalid: float = 0.0,
                  p_lower: float = 0.0, alphabet: bytes = b"ACGT"):
     """Independent random reads with lengths uniform in [min_len, max_len].

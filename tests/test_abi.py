@@ -48,6 +48,8 @@ def test_error_strings_without_gpu(lib):
     # NULL arguments are rejected before any CUDA call
     assert L.mh_create(None, None) == mh.MH_EINVAL
     assert L.mh_count_kmers(None, None, 21, 2, None) == mh.MH_EINVAL
+    assert L.mh_run_batch(None, None, 0, 31, 2, 1, 0, None) == mh.MH_EINVAL
+    assert L.mh_sort_shape(None) == -1
 
 
 def test_objects_are_sm103a():
