@@ -43,9 +43,22 @@ __global__ void __launch_bounds__(256) extract_canonical_kernel(const uint32_t* 
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const int K1 = k + 1;
+    // the next fragment's bounds load while this one is extracted
+    uint64_t b = 0, w0 = 0, w1 = 0;
+    if (warp < n_frags) {
+        b = frag_offs[warp];
+        w0 = woff[warp];
+        w1 = woff[warp + 1];
+    }
     for (uint64_t f = warp; f < n_frags; f += n_warps) {
-        uint64_t b = frag_offs[f];
-        uint64_t w0 = woff[f], nw = woff[f + 1] - w0;
+        const uint64_t fn = f + n_warps;
+        uint64_t nb = 0, nw0 = 0, nw1 = 0;
+        if (fn < n_frags) {
+            nb = frag_offs[fn];
+            nw0 = woff[fn];
+            nw1 = woff[fn + 1];
+        }
+        const uint64_t nw = w1 - w0;
         for (uint64_t i = lane; i < nw; i += 32) {
             Key<NW> x = load_window<NW>(packed, b + i, K1);
             Key<NW> r = key_rc<NW>(x, K1);
@@ -53,6 +66,9 @@ __global__ void __launch_bounds__(256) extract_canonical_kernel(const uint32_t* 
             if constexpr (MIXED) c = mix_key<NW>(c);
             store_key<NW>(out, w0 + i, c);
         }
+        b = nb;
+        w0 = nw0;
+        w1 = nw1;
     }
 }
 
@@ -593,7 +609,13 @@ void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, 
                   toff.p, keys.p, cnt.p, NW);
     big_k.reset();
     big_c.reset();
-    bool in_alt = radix_sort<NW>(ctx, keys.p, alt.p, cnt.p, calt.p, S, 0, 2 * K1);
+    // the table's keys are distinct and, as (k+1)-mers of both strands, their
+    // top bits spread: the spread order with counts attached (1-word keys)
+    bool in_alt;
+    if constexpr (NW == 1)
+        in_alt = radix_sort_spread_kv<1>(ctx, keys.p, alt.p, cnt.p, calt.p, S, 64 - 2 * K1);
+    else
+        in_alt = radix_sort<NW>(ctx, keys.p, alt.p, cnt.p, calt.p, S, 0, 2 * K1);
     if (in_alt) {
         out_keys = std::move(alt);
         out_cnt = std::move(calt);

@@ -594,6 +594,9 @@ bool radix_sort(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint
 // keys that share them.  The top `skip` bits must be equal in every key.
 template <int NW>
 bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n, int skip = 0);
+template <int NW>
+bool radix_sort_spread_kv(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt, uint64_t n,
+                          int skip);
 
 // ---------------------------------------------------------------- scans
 // out[i] = sum of in[0..i-1] for i in [0, n]; out has n+1 entries.

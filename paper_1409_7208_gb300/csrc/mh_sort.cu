@@ -418,6 +418,131 @@ __global__ void __launch_bounds__(256) spread_big_kernel(uint64_t* __restrict__ 
     }
 }
 
+// Key-value fix-up (distinct keys with a 32-bit payload): groups of up to
+// 16 keys are sorted by one thread each, pairs moving together; every other
+// group with a descent goes to a list, each listed group then to a segment
+// sort of its own (few, for spread keys).
+template <int NW>
+__global__ void __launch_bounds__(256) spread_fix_kv_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                            uint64_t n, int lo, uint64_t* __restrict__ big,
+                                                            uint64_t big_cap, unsigned long long* __restrict__ n_big) {
+    using F = Fix<NW>;
+    __shared__ uint64_t K[F::kWin * NW];
+    __shared__ uint32_t V[F::kWin];
+    __shared__ uint32_t head[F::kWords], desc[F::kWords];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t s = blockIdx.x * (uint64_t)F::kTile;
+    const uint32_t W = (uint32_t)(n - s < (uint64_t)F::kWin ? n - s : (uint64_t)F::kWin);
+    const uint32_t len = W < (uint32_t)F::kTile ? W : (uint32_t)F::kTile;
+    const bool window_ends_array = s + W == n;
+    auto kget = [&](uint32_t i) {
+        Key<NW> r;
+#pragma unroll
+        for (int w = 0; w < NW; w++) r.w[w] = K[i * NW + w];
+        return r;
+    };
+    auto kset = [&](uint32_t i, const Key<NW>& x) {
+#pragma unroll
+        for (int w = 0; w < NW; w++) K[i * NW + w] = x.w[w];
+    };
+    for (uint32_t i = tid; i < W * NW; i += 256) K[i] = keys[s * NW + i];
+    for (uint32_t i = tid; i < W; i += 256) V[i] = vals[s + i];
+    __syncthreads();
+    const uint64_t same_top = 1ull << lo;
+    for (uint32_t wd = warp; wd < (uint32_t)F::kWords; wd += 8) {
+        const uint32_t i = wd * 32 + lane;
+        bool h = false, d = false;
+        if (i < W) {
+            const Key<NW> x = kget(i);
+            const Key<NW> y = i > 0 ? kget(i - 1) : (s > 0 ? load_key<NW>(keys, s - 1) : key_ones<NW>());
+            h = i == 0 && s == 0 ? true : (x.w[NW - 1] ^ y.w[NW - 1]) >= same_top;
+            d = i > 0 && !h && key_less<NW>(x, y);
+        }
+        const uint32_t hb = __ballot_sync(0xFFFFFFFFu, h), db = __ballot_sync(0xFFFFFFFFu, d);
+        if (lane == 0) {
+            head[wd] = hb;
+            desc[wd] = db;
+        }
+    }
+    __syncthreads();
+    constexpr int PER = 8 / NW;
+    uint32_t hm = tid * PER < len ? (head[(tid * PER) >> 5] >> ((tid * PER) & 31)) & ((1u << PER) - 1u) : 0u;
+    if (tid * PER + PER > len) hm &= (1u << (len > tid * PER ? len - tid * PER : 0)) - 1u;
+    while (hm) {
+        const uint32_t h = tid * PER + __ffs(hm) - 1;
+        hm &= hm - 1;
+        const uint32_t g1 = next_bit(head, h + 1, W);
+        const bool open = g1 == W && !window_ends_array;
+        if (!open && !any_bit(desc, h + 1, g1)) continue;
+        if (open || g1 - h > (uint32_t)F::kThreadSort) {
+            const unsigned long long q = atomicAdd(n_big, 1ull);
+            if (q < big_cap) big[q] = s + h;
+            continue;
+        }
+        for (uint32_t j = h + 1; j < g1; j++) {
+            const Key<NW> x = kget(j);
+            const uint32_t v = V[j];
+            uint32_t i = j;
+            while (i > h && key_less<NW>(x, kget(i - 1))) {
+                kset(i, kget(i - 1));
+                V[i] = V[i - 1];
+                i--;
+            }
+            kset(i, x);
+            V[i] = v;
+        }
+        for (uint32_t j = h; j < g1; j++) {
+            store_key<NW>(keys, s + j, kget(j));
+            vals[s + j] = V[j];
+        }
+    }
+}
+
+// A CTA per listed group start: the group's end (first key with other top
+// bits), and (start, end) out if the group holds a descent.
+template <int NW>
+__global__ void __launch_bounds__(256) spread_bounds_kernel(const uint64_t* __restrict__ keys, uint64_t n, int lo,
+                                                            const uint64_t* __restrict__ list, uint64_t n_list,
+                                                            ulonglong2* __restrict__ rest,
+                                                            unsigned long long* __restrict__ n_rest) {
+    __shared__ uint64_t s_end;
+    const int tid = threadIdx.x;
+    auto top = [&](uint64_t i) { return keys[i * NW + NW - 1] >> lo; };
+    for (uint64_t g = blockIdx.x; g < n_list; g += gridDim.x) {
+        const uint64_t gs = list[g];
+        if (tid == 0) {
+            const uint64_t px = top(gs);
+            uint64_t l = gs + 1, step = 1, h;
+            while (true) {
+                const uint64_t probe = l + step - 1;
+                if (probe >= n) {
+                    h = n;
+                    break;
+                }
+                if (top(probe) != px) {
+                    h = probe;
+                    break;
+                }
+                l = probe + 1;
+                step <<= 1;
+            }
+            while (l < h) {
+                const uint64_t mid = (l + h) / 2;
+                if (top(mid) == px) l = mid + 1; else h = mid;
+            }
+            s_end = l;
+        }
+        __syncthreads();
+        const uint64_t ge = s_end;
+        uint32_t d = 0;
+        for (uint64_t i = gs + 1 + tid; i < ge; i += 256)
+            d |= key_less<NW>(load_key<NW>(keys, i), load_key<NW>(keys, i - 1));
+        d = __syncthreads_or(d);
+        if (d && tid == 0) rest[atomicAdd(n_rest, 1ull)] = make_ulonglong2(gs, ge);
+        __syncthreads();
+    }
+}
+
 static int ceil_log2(uint64_t n) {
     int b = 0;
     while (b < 64 && (1ull << b) < n) b++;
@@ -479,6 +604,55 @@ bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n, i
     }
     return in_alt;
 }
+
+// Distinct keys with a 32-bit payload (a solid table and its counts): the
+// same spread order (passes over the top P bits of the top word below
+// `skip` constant bits, then the key-value fix-up).  Keys whose top bits are
+// crowded (more than 256 groups past the thread sorts) are sorted fully.
+// Returns true when the result is in alt / valt.
+template <int NW>
+bool radix_sort_spread_kv(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt, uint64_t n,
+                          int skip) {
+    using F = Fix<NW>;
+    const int P = spread_bits(n);
+    const int bits = 64 * NW;
+    if (n <= 1 || P + skip >= 64) return radix_sort<NW>(ctx, keys, alt, vals, valt, n, 0, bits - skip);
+    const int lo = 64 - skip - P;
+    const bool in_alt = radix_sort<NW>(ctx, keys, alt, vals, valt, n, bits - skip - P, bits - skip);
+    uint64_t* k = in_alt ? alt : keys;
+    uint64_t* ko = in_alt ? keys : alt;
+    uint32_t* v = in_alt ? valt : vals;
+    uint32_t* vo = in_alt ? vals : valt;
+    constexpr uint64_t kMaxSegments = 256;
+    Buf<uint64_t> list(ctx, kMaxSegments), cnt(ctx, 2);
+    cnt.zero();
+    MH_LAUNCH_B(ctx, "spread_fixup_kv", n * (8 * NW + 4), (unsigned)ceil_div(n, F::kTile), 256, 0,
+                spread_fix_kv_kernel<NW>, k, v, n, lo, list.p, kMaxSegments, (unsigned long long*)cnt.p);
+    uint64_t n_big = 0;
+    read_u64(ctx, cnt.p, &n_big, 1);
+    if (n_big > kMaxSegments) return in_alt != radix_sort<NW>(ctx, k, ko, v, vo, n, 0, bits - skip);
+    if (!n_big) return in_alt;
+    Buf<ulonglong2> rest(ctx, n_big);
+    MH_LAUNCH(ctx, "spread_bounds", (unsigned)n_big, 256, 0, spread_bounds_kernel<NW>, k, n, lo, list.p, n_big,
+              rest.p, (unsigned long long*)(cnt.p + 1));
+    uint64_t n_rest = 0;
+    read_u64(ctx, cnt.p + 1, &n_rest, 1);
+    if (!n_rest) return in_alt;
+    std::vector<ulonglong2> h(n_rest);
+    MH_CUDA(cudaMemcpyAsync(h.data(), rest.p, sizeof(ulonglong2) * n_rest, cudaMemcpyDeviceToHost, ctx->stream));
+    sync_and_check(ctx);
+    for (const ulonglong2& seg : h) {
+        const uint64_t len = seg.y - seg.x;
+        if (radix_sort<NW>(ctx, k + seg.x * NW, ko + seg.x * NW, v + seg.x, vo + seg.x, len, 0, bits - skip - P)) {
+            MH_CUDA(cudaMemcpyAsync(k + seg.x * NW, ko + seg.x * NW, len * 8 * NW, cudaMemcpyDeviceToDevice,
+                                    ctx->stream));
+            MH_CUDA(cudaMemcpyAsync(v + seg.x, vo + seg.x, len * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+    }
+    return in_alt;
+}
+
+template bool radix_sort_spread_kv<1>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*, uint64_t, int);
 
 template bool radix_sort_spread<1>(mh_ctx*, uint64_t*, uint64_t*, uint64_t, int);
 template bool radix_sort_spread<2>(mh_ctx*, uint64_t*, uint64_t*, uint64_t, int);
