@@ -158,6 +158,17 @@ __device__ __forceinline__ uint32_t next_bit(const uint32_t* b, uint32_t i, uint
     }
 }
 
+// Last set bit at or before i in b, or ~0u.
+__device__ __forceinline__ uint32_t prev_bit(const uint32_t* b, uint32_t i) {
+    int w = (int)(i >> 5);
+    uint32_t m = b[w] & (0xFFFFFFFFu >> (31 - (i & 31)));
+    while (true) {
+        if (m) return (uint32_t)w * 32 + 31 - __clz(m);
+        if (--w < 0) return ~0u;
+        m = b[w];
+    }
+}
+
 // Any set bit in [i, j)?
 __device__ __forceinline__ bool any_bit(const uint32_t* b, uint32_t i, uint32_t j) {
     return next_bit(b, i, j) < j;
@@ -233,36 +244,48 @@ __global__ void __launch_bounds__(256) spread_fix_kernel(uint64_t* __restrict__ 
         }
     }
     __syncthreads();
-    // groups starting in this tile: thread per 8 / NW positions, visiting their heads
-    constexpr int PER = 8 / NW;
-    uint32_t hm = tid * PER < len ? (head[(tid * PER) >> 5] >> ((tid * PER) & 31)) & ((1u << PER) - 1u) : 0u;
-    if (tid * PER + PER > len) hm &= (1u << (len > tid * PER ? len - tid * PER : 0)) - 1u;
-    while (hm) {
-        const uint32_t h = tid * PER + __ffs(hm) - 1;
-        hm &= hm - 1;
-        const uint32_t g1 = next_bit(head, h + 1, W);
-        if (g1 == W && !window_ends_array) {
-            // may run past the window: checked by a CTA of its own
-            const unsigned long long q = atomicAdd(n_big, 1ull);
-            if (q < big_cap) big[q] = s + h;
-            continue;
-        }
-        if (!any_bit(desc, h + 1, g1)) continue;
-        if (g1 - h <= (uint32_t)F::kThreadSort) {
-            for (uint32_t j = h + 1; j < g1; j++) {
-                const Key<NW> x = kget(j);
-                uint32_t i = j;
-                while (i > h && key_less<NW>(x, kget(i - 1))) {
-                    kset(i, kget(i - 1));
-                    i--;
-                }
-                kset(i, x);
+    // groups starting in this tile that hold a descent, each found from its
+    // first descent (a word of descent bits a thread; descents are few: a
+    // group holds two distinct keys only where keys collide on the top bits)
+    auto to_big = [&](uint32_t h) {
+        const unsigned long long q = atomicAdd(n_big, 1ull);
+        if (q < big_cap) big[q] = s + h;
+    };
+    if (tid == 0 && !window_ends_array) {
+        // the tile's last group, if it may run past the window with no descent
+        // inside it: checked by a CTA of its own
+        const uint32_t h = prev_bit(head, len - 1);
+        if (h != ~0u && next_bit(head, h + 1, W) == W && !any_bit(desc, h + 1, W)) to_big(h);
+    }
+    for (uint32_t wd = tid; wd < (uint32_t)F::kWords; wd += 256) {
+        uint32_t dm = desc[wd];
+        while (dm) {
+            const uint32_t jd = wd * 32 + __ffs(dm) - 1;
+            dm &= dm - 1;
+            const uint32_t h = prev_bit(head, jd);
+            if (h == ~0u || h >= len) continue;  // the group starts in another tile
+            if (any_bit(desc, h + 1, jd)) continue;  // not its first descent
+            const uint32_t g1 = next_bit(head, jd + 1, W);
+            if (g1 == W && !window_ends_array) {
+                to_big(h);  // may run past the window
+                continue;
             }
-            for (uint32_t j = h; j < g1; j++) store_key<NW>(keys, s + j, kget(j));
-        } else {
-            const uint32_t q = atomicAdd(&n_queue, 1u);
-            queue[2 * q] = h;
-            queue[2 * q + 1] = g1;
+            if (g1 - h <= (uint32_t)F::kThreadSort) {
+                for (uint32_t j = h + 1; j < g1; j++) {
+                    const Key<NW> x = kget(j);
+                    uint32_t i = j;
+                    while (i > h && key_less<NW>(x, kget(i - 1))) {
+                        kset(i, kget(i - 1));
+                        i--;
+                    }
+                    kset(i, x);
+                }
+                for (uint32_t j = h; j < g1; j++) store_key<NW>(keys, s + j, kget(j));
+            } else {
+                const uint32_t q = atomicAdd(&n_queue, 1u);
+                queue[2 * q] = h;
+                queue[2 * q + 1] = g1;
+            }
         }
     }
     __syncthreads();
@@ -465,35 +488,44 @@ __global__ void __launch_bounds__(256) spread_fix_kv_kernel(uint64_t* __restrict
         }
     }
     __syncthreads();
-    constexpr int PER = 8 / NW;
-    uint32_t hm = tid * PER < len ? (head[(tid * PER) >> 5] >> ((tid * PER) & 31)) & ((1u << PER) - 1u) : 0u;
-    if (tid * PER + PER > len) hm &= (1u << (len > tid * PER ? len - tid * PER : 0)) - 1u;
-    while (hm) {
-        const uint32_t h = tid * PER + __ffs(hm) - 1;
-        hm &= hm - 1;
-        const uint32_t g1 = next_bit(head, h + 1, W);
-        const bool open = g1 == W && !window_ends_array;
-        if (!open && !any_bit(desc, h + 1, g1)) continue;
-        if (open || g1 - h > (uint32_t)F::kThreadSort) {
-            const unsigned long long q = atomicAdd(n_big, 1ull);
-            if (q < big_cap) big[q] = s + h;
-            continue;
-        }
-        for (uint32_t j = h + 1; j < g1; j++) {
-            const Key<NW> x = kget(j);
-            const uint32_t v = V[j];
-            uint32_t i = j;
-            while (i > h && key_less<NW>(x, kget(i - 1))) {
-                kset(i, kget(i - 1));
-                V[i] = V[i - 1];
-                i--;
+    // groups found from their first descent, as in spread_fix_kernel
+    auto to_big = [&](uint32_t h) {
+        const unsigned long long q = atomicAdd(n_big, 1ull);
+        if (q < big_cap) big[q] = s + h;
+    };
+    if (tid == 0 && !window_ends_array) {
+        const uint32_t h = prev_bit(head, len - 1);
+        if (h != ~0u && next_bit(head, h + 1, W) == W && !any_bit(desc, h + 1, W)) to_big(h);
+    }
+    for (uint32_t wd = tid; wd < (uint32_t)F::kWords; wd += 256) {
+        uint32_t dm = desc[wd];
+        while (dm) {
+            const uint32_t jd = wd * 32 + __ffs(dm) - 1;
+            dm &= dm - 1;
+            const uint32_t h = prev_bit(head, jd);
+            if (h == ~0u || h >= len) continue;
+            if (any_bit(desc, h + 1, jd)) continue;
+            const uint32_t g1 = next_bit(head, jd + 1, W);
+            if ((g1 == W && !window_ends_array) || g1 - h > (uint32_t)F::kThreadSort) {
+                to_big(h);
+                continue;
             }
-            kset(i, x);
-            V[i] = v;
-        }
-        for (uint32_t j = h; j < g1; j++) {
-            store_key<NW>(keys, s + j, kget(j));
-            vals[s + j] = V[j];
+            for (uint32_t j = h + 1; j < g1; j++) {
+                const Key<NW> x = kget(j);
+                const uint32_t v = V[j];
+                uint32_t i = j;
+                while (i > h && key_less<NW>(x, kget(i - 1))) {
+                    kset(i, kget(i - 1));
+                    V[i] = V[i - 1];
+                    i--;
+                }
+                kset(i, x);
+                V[i] = v;
+            }
+            for (uint32_t j = h; j < g1; j++) {
+                store_key<NW>(keys, s + j, kget(j));
+                vals[s + j] = V[j];
+            }
         }
     }
 }
