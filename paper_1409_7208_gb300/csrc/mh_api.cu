@@ -261,6 +261,8 @@ void mh_destroy(mh_ctx* ctx) {
     cudaFree(ctx->d_status);
     cudaFreeHost(ctx->h_pinned);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    for (cudaEvent_t e : ctx->pack_ev)
+        if (e) cudaEventDestroy(e);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;

@@ -51,6 +51,7 @@ struct mh_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t copy_stream = nullptr;  // host uploads overlapped with packing (created on first use)
+    cudaEvent_t pack_ev[5] = {};         // the staged upload's events (created on first use)
     std::vector<mh_ctx*> workers;        // worker contexts of mh_run_batch (created on first use)
     int sort_shape = -1;                 // scatter tile shape for 1-word keys (-1: default)
     int tuned_k = -1;                    // k the shape was tuned at

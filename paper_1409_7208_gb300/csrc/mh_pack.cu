@@ -261,13 +261,15 @@ void pack_reads(mh_ctx* ctx, const uint8_t* d_ascii, uint64_t n_bases, const uin
     out->frag_read = fr.release();
 }
 
-// Reads in host memory (pinned for overlap): the ASCII streams through two
-// device staging buffers of kPiece bytes on the context's copy stream while
-// the context stream packs the piece before (piece starts are multiples of
-// 16 bases, so every piece fills whole packed words of its own).  Only the
-// packed stream and the offsets stay on the device.  If some byte is not a
-// base or some read is empty, the fragments must be found and the bases
-// compacted: the ASCII is then uploaded whole and packed as from the device.
+// Reads in host memory (pinned for overlap): up to one piece (kPiece bytes)
+// is uploaded on the context stream and packed as from the device.  Larger
+// inputs stream through two device staging buffers of kPiece bytes on the
+// context's copy stream while the context stream packs the piece before
+// (piece starts are multiples of 16 bases, so every piece fills whole
+// packed words of its own); only the packed stream and the offsets stay on
+// the device.  If some byte is not a base or some read is empty, the
+// fragments must be found and the bases compacted: the ASCII is then
+// uploaded whole and packed as from the device.
 constexpr uint64_t kPiece = 256ull << 20;
 
 // staging piece in bytes: kPiece, or MH_PACK_PIECE (a multiple of 16; tests)
@@ -287,23 +289,30 @@ static cudaStream_t copy_stream(mh_ctx* ctx) {
 
 void pack_reads_host(mh_ctx* ctx, const uint8_t* h_ascii, uint64_t n_bases, const uint64_t* h_offs, uint64_t n_reads,
                      mh_reads* out) {
+    if (n_bases <= piece_bytes()) {
+        // one piece: a plain upload on the context stream, then the device path
+        Buf<uint8_t> da(ctx, n_bases + 16);
+        Buf<uint64_t> doff(ctx, n_reads + 1);
+        if (n_bases) MH_CUDA(cudaMemcpyAsync(da.p, h_ascii, n_bases, cudaMemcpyHostToDevice, ctx->stream));
+        MH_CUDA(cudaMemcpyAsync(doff.p, h_offs, sizeof(uint64_t) * (n_reads + 1), cudaMemcpyHostToDevice,
+                                ctx->stream));
+        pack_reads(ctx, da.p, n_bases, doff.p, n_reads, out);
+        return;
+    }
     cudaStream_t cs = copy_stream(ctx);
     const uint64_t n_chunks = ceil_div(n_bases, 16);
-    const uint64_t piece = n_bases < piece_bytes() ? ceil_div(n_bases ? n_bases : 1, 16) * 16 : piece_bytes();
+    const uint64_t piece = piece_bytes();
     const uint64_t n_pieces = ceil_div(n_bases, piece);
     Buf<uint64_t> doff(ctx, n_reads + 1);
     Buf<uint32_t> flags(ctx, 2);  // [0] any invalid byte, [1] any empty read
     flags.zero();
     Buf<uint32_t> packed(ctx, n_chunks + kPackPad);
     MH_CUDA(cudaMemsetAsync(packed.p + n_chunks, 0, kPackPad * sizeof(uint32_t), ctx->stream));
-    Buf<uint8_t> stage[2] = {Buf<uint8_t>(ctx, n_pieces ? piece : 1), Buf<uint8_t>(ctx, n_pieces > 1 ? piece : 1)};
-    cudaEvent_t ev[5] = {};
-    auto done = [&] {
-        for (auto e : ev)
-            if (e) cudaEventDestroy(e);
-    };
-    try {
-        for (auto& e : ev) MH_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    Buf<uint8_t> stage[2] = {Buf<uint8_t>(ctx, piece), Buf<uint8_t>(ctx, piece)};
+    cudaEvent_t* ev = ctx->pack_ev;  // created once a context
+    for (int i = 0; i < 5; i++)
+        if (!ev[i]) MH_CUDA(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+    {
         // the copy stream writes buffers just allocated on the context stream
         MH_CUDA(cudaEventRecord(ev[4], ctx->stream));
         MH_CUDA(cudaStreamWaitEvent(cs, ev[4], 0));
@@ -323,11 +332,7 @@ void pack_reads_host(mh_ctx* ctx, const uint8_t* h_ascii, uint64_t n_bases, cons
                       stage[s].p, len, true, packed.p + b / 16, flags.p);
             MH_CUDA(cudaEventRecord(ev[2 + s], ctx->stream));
         }
-    } catch (...) {
-        done();
-        throw;
     }
-    done();
     stage[0].reset();
     stage[1].reset();
     uint64_t fl[1];

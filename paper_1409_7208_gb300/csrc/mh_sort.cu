@@ -441,10 +441,12 @@ __global__ void __launch_bounds__(256) spread_big_kernel(uint64_t* __restrict__ 
     }
 }
 
-// Key-value fix-up (distinct keys with a 32-bit payload): groups of up to
-// 16 keys are sorted by one thread each, pairs moving together; every other
-// group with a descent goes to a list, each listed group then to a segment
-// sort of its own (few, for spread keys).
+// Key-value fix-up (keys with a 32-bit payload): groups of up to 16 keys
+// are sorted by one thread each, pairs moving together; larger groups inside
+// the window by one warp (successive minima: each round writes every copy
+// of the smallest key above the previous one with its payloads); groups that
+// run past the window or hold more than 64 distinct keys go to a list, each
+// listed group then to a segment sort of its own (few, for spread keys).
 template <int NW>
 __global__ void __launch_bounds__(256) spread_fix_kv_kernel(uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                             uint64_t n, int lo, uint64_t* __restrict__ big,
@@ -453,6 +455,8 @@ __global__ void __launch_bounds__(256) spread_fix_kv_kernel(uint64_t* __restrict
     __shared__ uint64_t K[F::kWin * NW];
     __shared__ uint32_t V[F::kWin];
     __shared__ uint32_t head[F::kWords], desc[F::kWords];
+    __shared__ uint32_t queue[2 * F::kQueue];  // (start, end) of the groups for warps
+    __shared__ uint32_t n_queue;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t s = blockIdx.x * (uint64_t)F::kTile;
     const uint32_t W = (uint32_t)(n - s < (uint64_t)F::kWin ? n - s : (uint64_t)F::kWin);
@@ -470,6 +474,7 @@ __global__ void __launch_bounds__(256) spread_fix_kv_kernel(uint64_t* __restrict
     };
     for (uint32_t i = tid; i < W * NW; i += 256) K[i] = keys[s * NW + i];
     for (uint32_t i = tid; i < W; i += 256) V[i] = vals[s + i];
+    if (tid == 0) n_queue = 0;
     __syncthreads();
     const uint64_t same_top = 1ull << lo;
     for (uint32_t wd = warp; wd < (uint32_t)F::kWords; wd += 8) {
@@ -506,8 +511,14 @@ __global__ void __launch_bounds__(256) spread_fix_kv_kernel(uint64_t* __restrict
             if (h == ~0u || h >= len) continue;
             if (any_bit(desc, h + 1, jd)) continue;
             const uint32_t g1 = next_bit(head, jd + 1, W);
-            if ((g1 == W && !window_ends_array) || g1 - h > (uint32_t)F::kThreadSort) {
+            if (g1 == W && !window_ends_array) {
                 to_big(h);
+                continue;
+            }
+            if (g1 - h > (uint32_t)F::kThreadSort) {
+                const uint32_t q = atomicAdd(&n_queue, 1u);
+                queue[2 * q] = h;
+                queue[2 * q + 1] = g1;
                 continue;
             }
             for (uint32_t j = h + 1; j < g1; j++) {
@@ -526,6 +537,59 @@ __global__ void __launch_bounds__(256) spread_fix_kv_kernel(uint64_t* __restrict
                 store_key<NW>(keys, s + j, kget(j));
                 vals[s + j] = V[j];
             }
+        }
+    }
+    __syncthreads();
+    // larger groups: a warp each, from K and V to keys and vals
+    const uint32_t nq = n_queue;
+    for (uint32_t q = warp; q < nq; q += 8) {
+        const uint32_t g0 = queue[2 * q], g1 = queue[2 * q + 1];
+        uint32_t pos = g0;
+        Key<NW> prev = key_zero<NW>();
+        bool first = true;
+        int rounds = 0;
+        while (pos < g1 && rounds < kFixWarpRounds) {
+            Key<NW> mn = key_ones<NW>();
+            bool have = false;
+            for (uint32_t i = g0 + lane; i < g1; i += 32) {
+                const Key<NW> x = kget(i);
+                if ((first || key_less<NW>(prev, x)) && (!have || key_less<NW>(x, mn))) {
+                    mn = x;
+                    have = true;
+                }
+            }
+            for (int off = 16; off; off >>= 1) {
+                const Key<NW> o = shfl_key<NW>(mn, off);
+                const bool oh = __shfl_xor_sync(0xFFFFFFFFu, have, off);
+                if (oh && (!have || key_less<NW>(o, mn))) {
+                    mn = o;
+                    have = true;
+                }
+            }
+            // every copy of mn, with its payload, in group order
+            for (uint32_t b0 = g0; b0 < g1; b0 += 32) {
+                const uint32_t i = b0 + lane;
+                const bool eq = i < g1 && key_eq<NW>(kget(i), mn);
+                const uint32_t m = __ballot_sync(0xFFFFFFFFu, eq);
+                if (eq) {
+                    const uint32_t o = pos + __popc(m & ((1u << lane) - 1u));
+                    store_key<NW>(keys, s + o, mn);
+                    vals[s + o] = V[i];
+                }
+                pos += __popc(m);
+            }
+            prev = mn;
+            first = false;
+            rounds++;
+        }
+        __syncwarp();
+        if (pos < g1) {
+            // too many distinct keys: rewrite the group as it was and defer it
+            for (uint32_t i = g0 + lane; i < g1; i += 32) {
+                store_key<NW>(keys, s + i, kget(i));
+                vals[s + i] = V[i];
+            }
+            if (lane == 0) to_big(g0);
         }
     }
 }
@@ -648,7 +712,14 @@ bool radix_sort_spread_kv(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* 
     using F = Fix<NW>;
     const int P = spread_bits(n);
     const int bits = 64 * NW;
-    if (n <= 1 || P + skip >= 64) return radix_sort<NW>(ctx, keys, alt, vals, valt, n, 0, bits - skip);
+    // small tables (below 2^20 keys, or MH_SPREAD_KV_MIN for tests): the full
+    // sort, which needs no read-back of the fix-up's list
+    static const uint64_t kv_min = [] {
+        const char* e = std::getenv("MH_SPREAD_KV_MIN");
+        return e ? (uint64_t)std::strtoull(e, nullptr, 10) : (uint64_t)1 << 20;
+    }();
+    if (n < std::max<uint64_t>(kv_min, 2) || P + skip >= 64)
+        return radix_sort<NW>(ctx, keys, alt, vals, valt, n, 0, bits - skip);
     const int lo = 64 - skip - P;
     const bool in_alt = radix_sort<NW>(ctx, keys, alt, vals, valt, n, bits - skip - P, bits - skip);
     uint64_t* k = in_alt ? alt : keys;

@@ -5,7 +5,8 @@ between chunks; 1 or 3 tiles per chunk), and the count sort's fix-up of
 keys sharing their top bits (passes over the top 8, 16 or 24 bits only, so
 that groups of every size occur: a few keys sorted by one thread, tens to
 thousands by a warp or a CTA, and crowded groups by the segment fallback),
-the out-of-core count (2 or 16 buckets of keys counted one at a time,
+the key-value form of the spread order for solid tables (thread, warp and
+segment sorts of groups), the out-of-core count (2 or 16 buckets of keys counted one at a time,
 spectra concatenated, solid tables merged), and reads streamed from host
 memory through staging pieces of 48 bytes or 4 KB (pieces that end inside a
 read, reads that span several pieces, invalid bytes found mid-stream)."""
@@ -58,10 +59,13 @@ print("ok")
 @pytest.mark.parametrize("var,val", [("MH_SORT_CHUNK_TILES", "1"), ("MH_SORT_CHUNK_TILES", "3"),
                                      ("MH_SPREAD_BITS", "8"), ("MH_SPREAD_BITS", "16"),
                                      ("MH_SPREAD_BITS", "24"), ("MH_COUNT_BUCKET_BITS", "1"),
-                                     ("MH_COUNT_BUCKET_BITS", "4"), ("MH_PACK_PIECE", "48"),
+                                     ("MH_COUNT_BUCKET_BITS", "4"), ("MH_SPREAD_KV_MIN", "0"),
+                                     ("MH_PACK_PIECE", "48"),
                                      ("MH_PACK_PIECE", "4096")])
 def test_small_input_paths_match_oracle(var, val):
-    env = dict(os.environ, **{var: val})
+    # every run also sorts the small solid tables by the spread key-value path
+    env = dict(os.environ, MH_SPREAD_KV_MIN="0")
+    env[var] = val
     p = subprocess.run([sys.executable, "-c", CHILD], env=env, capture_output=True, text=True, timeout=600)
     assert p.returncode == 0, p.stdout + p.stderr
     assert "ok" in p.stdout
