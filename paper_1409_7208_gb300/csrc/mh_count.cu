@@ -33,12 +33,22 @@ __global__ void frag_windows_kernel(const uint64_t* __restrict__ frag_offs, uint
 }
 
 // Warp per fragment: canonical key of every window, written at woff[f] + i
-// (MIXED: its mix_bij image, 1-word keys).
+// (MIXED: its mix_bij image, 1-word keys).  With `hist`, the block also
+// counts the digits the sort's passes will use (n_passes digits of 8 bits
+// from bit shift0; in dynamic shared memory, added to hist at the end), so
+// the sort needs no histogram pass of its own.
 template <int NW, bool MIXED>
 __global__ void __launch_bounds__(256) extract_canonical_kernel(const uint32_t* __restrict__ packed,
                                                                 const uint64_t* __restrict__ frag_offs,
                                                                 const uint64_t* __restrict__ woff, uint64_t n_frags,
-                                                                int k, uint64_t* __restrict__ out) {
+                                                                int k, uint64_t* __restrict__ out,
+                                                                uint32_t* __restrict__ hist, int shift0,
+                                                                int n_passes) {
+    extern __shared__ uint32_t sh[];
+    if (hist) {
+        for (int i = threadIdx.x; i < n_passes * 256; i += blockDim.x) sh[i] = 0;
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -65,10 +75,17 @@ __global__ void __launch_bounds__(256) extract_canonical_kernel(const uint32_t* 
             Key<NW> c = key_less<NW>(r, x) ? r : x;
             if constexpr (MIXED) c = mix_key<NW>(c);
             store_key<NW>(out, w0 + i, c);
+            if (hist)
+                for (int p = 0; p < n_passes; p++) atomicAdd(&sh[p * 256 + key_digit<NW>(c, shift0 + 8 * p)], 1u);
         }
         b = nb;
         w0 = nw0;
         w1 = nw1;
+    }
+    if (hist) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < n_passes * 256; i += blockDim.x)
+            if (sh[i]) atomicAdd(&hist[i], sh[i]);
     }
 }
 
@@ -682,12 +699,20 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
     const int bb = count_bucket_bits(ctx, n, NW);
     if (bb == 0) {
         Buf<uint64_t> keys(ctx, (n ? n : 1) * NW), alt(ctx, (n ? n : 1) * NW);
+        // the extraction counts the digits of the spread sort's passes
+        const int P = spread_pass_bits(n);
+        const bool fuse = n > 1 && P < 64;
+        const int n_passes = (P + 7) / 8;
+        Buf<uint32_t> hist(ctx, fuse ? (size_t)n_passes * 256 : 1);
+        if (fuse) hist.zero();
         if (n)
             MH_LAUNCH_B(ctx, "extract_canonical", reads->n_packed / 4 + n * 8 * NW, grid_for(ctx, F * 32, 256, 8),
-                        256, 0, (extract_canonical_kernel<NW, kMixed>), reads->packed, reads->frag_offs, woff.p, F, k,
-                        keys.p);
+                        256, fuse ? sizeof(uint32_t) * n_passes * 256 : 0, (extract_canonical_kernel<NW, kMixed>),
+                        reads->packed, reads->frag_offs, woff.p, F, k, keys.p, fuse ? hist.p : nullptr,
+                        64 * NW - P, n_passes);
         woff.reset();
-        bool in_alt = radix_sort_spread<NW>(ctx, keys.p, alt.p, n);
+        bool in_alt = radix_sort_spread<NW>(ctx, keys.p, alt.p, n, 0, fuse ? hist.p : nullptr);
+        hist.reset();
         Buf<uint64_t>& sorted = in_alt ? alt : keys;
         Buf<uint64_t>& other = in_alt ? keys : alt;
         Buf<uint64_t> sk;

@@ -582,19 +582,22 @@ __device__ __forceinline__ uint64_t key_hash(const Key<NW>& a) {
 // LSD radix sort (one digit histogram pass, then one onesweep pass per
 // 8-bit digit of bits [bit_lo, bit_hi)).  keys/alt (and vals/valt when
 // vals != nullptr) are n-element buffers; returns true if the sorted data
-// ended in alt/valt, false if in keys/vals.
+// ended in alt/valt, false if in keys/vals.  `hist`, when given, holds the
+// digit counts of the passes (pass p's 256 counts at p * 256), counted by
+// the caller while it wrote the keys; the histogram pass is then skipped.
 template <int NW>
 bool radix_sort(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt, uint64_t n,
-                int bit_lo, int bit_hi);
+                int bit_lo, int bit_hi, const uint32_t* hist = nullptr);
 
-// Sort 1-word keys ascending when their values are spread uniformly (mixed
-// k-mers): LSD passes over the top P = ceil(log2 n) + 8 bits only (whole
-// digits), then the rare groups of distinct keys sharing those bits are put
-// in order.  Returns true if the result is in alt.
-// Sort of mix_key images: passes over the top bits only, then a fix-up of
-// keys that share them.  The top `skip` bits must be equal in every key.
+// Sort of mix_key images (evenly spread top bits): LSD passes over the top
+// P = spread_pass_bits(n) bits below the top `skip` bits (equal in every
+// key), then a fix-up of the keys that share them.  `hist`: the counts of
+// those passes' digits (as for radix_sort), or nullptr.  Returns true if the
+// result is in alt.
+int spread_pass_bits(uint64_t n);
 template <int NW>
-bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n, int skip = 0);
+bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n, int skip = 0,
+                       const uint32_t* hist = nullptr);
 template <int NW>
 bool radix_sort_spread_kv(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt, uint64_t n,
                           int skip);

@@ -33,19 +33,22 @@ static uint64_t chunk_tiles() {
 
 template <int NW, bool HV, int ITEMS, int MINB>
 static bool radix_sort_impl(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt, uint64_t n,
-                            int bit_lo, int bit_hi) {
+                            int bit_lo, int bit_hi, const uint32_t* hist_in) {
     if (n <= 1 || bit_hi <= bit_lo) return false;
     constexpr int TILE = sort_tile<NW, ITEMS>();
     const int n_passes = (bit_hi - bit_lo + 7) / 8;
     const uint64_t chunk_len = chunk_tiles() * TILE;
     const int n_chunks = (int)ceil_div(n, chunk_len);
-    Buf<uint32_t> hist(ctx, (size_t)n_passes * 256);
+    Buf<uint32_t> hist(ctx, hist_in ? 1 : (size_t)n_passes * 256);
     // base[(p * n_chunks + c) * 256 + d]: where chunk c of pass p starts writing digit d
     Buf<uint64_t> base(ctx, (size_t)n_passes * n_chunks * 256);
-    hist.zero();
-    MH_LAUNCH_B(ctx, "radix_hist", n * 8 * NW, grid_for(ctx, n, 256, 8), 256, sizeof(uint32_t) * n_passes * 256,
-                radix_hist_kernel<NW>, keys, n, bit_lo, n_passes, hist.p);
-    MH_LAUNCH(ctx, "radix_base", n_passes, 256, 0, radix_base_kernel, hist.p, base.p, (uint64_t)n_chunks * 256);
+    if (!hist_in) {
+        hist.zero();
+        MH_LAUNCH_B(ctx, "radix_hist", n * 8 * NW, grid_for(ctx, n, 256, 8), 256, sizeof(uint32_t) * n_passes * 256,
+                    radix_hist_kernel<NW>, keys, n, bit_lo, n_passes, hist.p);
+    }
+    MH_LAUNCH(ctx, "radix_base", n_passes, 256, 0, radix_base_kernel, hist_in ? hist_in : hist.p, base.p,
+              (uint64_t)n_chunks * 256);
     const uint64_t max_tiles = std::min<uint64_t>(chunk_tiles(), ceil_div(n, TILE));
     Buf<uint32_t> status(ctx, max_tiles * 256);
     Buf<uint32_t> counter(ctx, 64);
@@ -88,31 +91,31 @@ static int sort_variant() {
 
 template <int NW, bool HV>
 static bool radix_sort_dispatch(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt,
-                                uint64_t n, int bit_lo, int bit_hi) {
+                                uint64_t n, int bit_lo, int bit_hi, const uint32_t* h) {
     if constexpr (NW == 1) {
         if constexpr (HV) {
-            return radix_sort_impl<NW, HV, 12, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
+            return radix_sort_impl<NW, HV, 12, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h);
         } else {
             switch (ctx->sort_shape >= 0 ? ctx->sort_shape : sort_variant()) {
-                case 1: return radix_sort_impl<NW, HV, 14, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
-                case 2: return radix_sort_impl<NW, HV, 12, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
-                default: return radix_sort_impl<NW, HV, 12, 4>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
+                case 1: return radix_sort_impl<NW, HV, 14, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h);
+                case 2: return radix_sort_impl<NW, HV, 12, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h);
+                default: return radix_sort_impl<NW, HV, 12, 4>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h);
             }
         }
     }
-    return radix_sort_impl<NW, HV, SortItems<NW>::v, 2>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
+    return radix_sort_impl<NW, HV, SortItems<NW>::v, 2>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h);
 }
 
 template <int NW>
 bool radix_sort(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt, uint64_t n, int bit_lo,
-                int bit_hi) {
-    if (vals) return radix_sort_dispatch<NW, true>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi);
-    return radix_sort_dispatch<NW, false>(ctx, keys, alt, nullptr, nullptr, n, bit_lo, bit_hi);
+                int bit_hi, const uint32_t* hist) {
+    if (vals) return radix_sort_dispatch<NW, true>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, hist);
+    return radix_sort_dispatch<NW, false>(ctx, keys, alt, nullptr, nullptr, n, bit_lo, bit_hi, hist);
 }
 
-template bool radix_sort<1>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*, uint64_t, int, int);
-template bool radix_sort<2>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*, uint64_t, int, int);
-template bool radix_sort<4>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*, uint64_t, int, int);
+template bool radix_sort<1>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*, uint64_t, int, int, const uint32_t*);
+template bool radix_sort<2>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*, uint64_t, int, int, const uint32_t*);
+template bool radix_sort<4>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*, uint64_t, int, int, const uint32_t*);
 
 // ------------------------------------------------------------ spread sort
 // The keys are mix_key images, so the top bits of their top word are evenly
@@ -656,15 +659,17 @@ static int spread_bits(uint64_t n) {
     return forced ? forced : std::max(8, ((ceil_log2(n) + 7) / 8) * 8);
 }
 
+int spread_pass_bits(uint64_t n) { return spread_bits(n); }
+
 template <int NW>
-bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n, int skip) {
+bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n, int skip, const uint32_t* hist) {
     using F = Fix<NW>;
     const int P = spread_bits(n);
     const int bits = 64 * NW;
     if (n <= 1 || P + skip >= 64) return radix_sort<NW>(ctx, keys, alt, nullptr, nullptr, n, 0, bits - skip);
     // the top `skip` bits are equal in every key: passes over the P bits below
     const int lo = 64 - skip - P;  // within the top word
-    const bool in_alt = radix_sort<NW>(ctx, keys, alt, nullptr, nullptr, n, bits - skip - P, bits - skip);
+    const bool in_alt = radix_sort<NW>(ctx, keys, alt, nullptr, nullptr, n, bits - skip - P, bits - skip, hist);
     uint64_t* k = in_alt ? alt : keys;
     uint64_t* other = in_alt ? keys : alt;
     const uint64_t cap = std::max<uint64_t>(1 << 16, n / 64);
@@ -757,9 +762,9 @@ bool radix_sort_spread_kv(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* 
 
 template bool radix_sort_spread_kv<1>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*, uint64_t, int);
 
-template bool radix_sort_spread<1>(mh_ctx*, uint64_t*, uint64_t*, uint64_t, int);
-template bool radix_sort_spread<2>(mh_ctx*, uint64_t*, uint64_t*, uint64_t, int);
-template bool radix_sort_spread<4>(mh_ctx*, uint64_t*, uint64_t*, uint64_t, int);
+template bool radix_sort_spread<1>(mh_ctx*, uint64_t*, uint64_t*, uint64_t, int, const uint32_t*);
+template bool radix_sort_spread<2>(mh_ctx*, uint64_t*, uint64_t*, uint64_t, int, const uint32_t*);
+template bool radix_sort_spread<4>(mh_ctx*, uint64_t*, uint64_t*, uint64_t, int, const uint32_t*);
 
 // ------------------------------------------------------------------ scans
 constexpr int kScanThreads = 256;
