@@ -653,12 +653,12 @@ template void expand_runs<4>(mh_ctx*, const uint64_t*, uint64_t, int, int, Buf<u
                              RunList*);
 
 // Buckets of the mixed canonical keys to count one at a time (0 = all at
-// once): with an HBM budget, enough that one bucket's working set (keys,
-// sort buffer, run slots: about 24 nw + 12 bytes a window), with the byte a
-// window of bucket numbers, takes at most 60%
-// of the budget still free (up to 64 buckets); without a budget, of 85% of
-// the device's memory.  MH_COUNT_BUCKET_BITS (0..6)
-// forces it (tests).
+// once).  Memory still free: the HBM budget, or without one 85% of the
+// device's memory, less what the context holds.  All at once if the count's
+// working set (keys, sort buffer, run slots: about 24 nw + 12 bytes a
+// window) fits in 90% of it; otherwise enough buckets (up to 64) that one
+// bucket's working set and the byte a window of bucket numbers take at most
+// 60% of it.  MH_COUNT_BUCKET_BITS (0..6) forces the number (tests).
 static int count_bucket_bits(mh_ctx* ctx, uint64_t n, int nw) {
     static const int forced = [] {
         const char* e = std::getenv("MH_COUNT_BUCKET_BITS");
@@ -670,9 +670,12 @@ static int count_bucket_bits(mh_ctx* ctx, uint64_t n, int nw) {
     const double per = 24.0 * nw + 12.0;
     const uint64_t budget = ctx->budget ? ctx->budget : ctx->device_bytes / 20 * 17;
     const double avail = budget > ctx->in_use ? (double)(budget - ctx->in_use) : 0.0;
-    // bucketed, one byte a window (its bucket) stays for the whole count
-    auto need = [&](int bb) { return (bb ? (double)n : 0.0) + (double)n / (double)(1ull << bb) * 1.05 * per; };
-    int bb = 0;
+    // in memory if the whole count fits in 90% of what is free; bucketed, the
+    // buckets' outputs accumulate beside the next bucket's working set, and
+    // one byte a window (its bucket) stays for the whole count
+    if ((double)n * 1.05 * per <= 0.9 * avail) return 0;
+    auto need = [&](int bb) { return (double)n + (double)n / (double)(1ull << bb) * 1.05 * per; };
+    int bb = 1;
     while (bb < 6 && need(bb) > 0.6 * avail) bb++;
     return bb;
 }
@@ -699,9 +702,10 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
     const int bb = count_bucket_bits(ctx, n, NW);
     if (bb == 0) {
         Buf<uint64_t> keys(ctx, (n ? n : 1) * NW), alt(ctx, (n ? n : 1) * NW);
-        // the extraction counts the digits of the spread sort's passes
+        // the extraction counts the digits of the spread sort's passes (1-word
+        // keys: for wider keys it measured no faster than the histogram pass)
         const int P = spread_pass_bits(n);
-        const bool fuse = n > 1 && P < 64;
+        const bool fuse = NW == 1 && n > 1 && P < 64;
         const int n_passes = (P + 7) / 8;
         Buf<uint32_t> hist(ctx, fuse ? (size_t)n_passes * 256 : 1);
         if (fuse) hist.zero();
