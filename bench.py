@@ -493,19 +493,37 @@ def run_batched(args, rank, world, local):
 
 
 SERVED = {
-    "name": "served: Poisson arrivals (20/s) for 15 s of count+mercy+build jobs; reads per job lognormal "
-            "(median 20k, sigma ln(2000)/4) clipped to [2k, 1M] (the served config's distribution scaled by "
-            "1/22); read length uniform 100-150 bp; k uniform over {21,31,41,61}; d=2; each job's reads from "
-            "its own uniform genome at 20x with 0.5% errors; 4 slots under an HBM budget of 150 GB",
-    "rate": 20.0, "secs": 15.0, "median": 20_000, "sigma": 1.9002, "lo": 2_000, "hi": 1_000_000,
-    "ks": (21, 31, 41, 61), "slots": 4, "budget": 150 << 30, "seed": 5,
+    "name": "served: Poisson arrivals (20/s) for 60 s of count+mercy+build jobs; reads per job lognormal "
+            "(median 447k, sigma ln(2000)/4) clipped to [10k, 20M]; read length uniform 100-150 bp; k uniform "
+            "over {21,31,41,61}; d=2; reads of each job from a uniform genome at 20x with 0.5% errors, drawn "
+            "from a pool of 96 distinct read sets in pinned host memory; 4 slots under an HBM budget of 150 GB",
+    "rate": 20.0, "secs": 60.0, "median": 447_000, "sigma": 1.9002, "lo": 10_000, "hi": 20_000_000,
+    "ks": (21, 31, 41, 61), "slots": 4, "budget": 150 << 30, "seed": 5, "pool": 96,
 }
 
 
-def _served_jobs(seed, secs):
+def _served_pool(seed):
+    """The distinct read sets the jobs draw from: sizes from the served
+    distribution, each its own uniform genome at 20x, in pinned host memory."""
     import numpy as np
+    import torch
 
     import synth
+    rng = np.random.default_rng(seed)
+    pool = []
+    for i in range(SERVED["pool"]):
+        n = int(np.clip(rng.lognormal(np.log(SERVED["median"]), SERVED["sigma"]), SERVED["lo"], SERVED["hi"]))
+        L = int(rng.integers(100, 151))
+        ascii, offs = synth.uniform_genome_reads(int(rng.integers(1 << 30)), max(5000, n * L // 20), n, L, 0.005)
+        pool.append((torch.from_numpy(ascii).pin_memory().numpy(), offs))
+    return pool
+
+
+def _served_jobs(pool, seed, secs):
+    """Poisson arrivals over `secs` seconds; each job a pool read set (drawn
+    uniformly) with k drawn uniformly."""
+    import numpy as np
+
     from paper_1409_7208_gb300 import serve
     rng = np.random.default_rng(seed)
     t, jobs = 0.0, []
@@ -513,10 +531,8 @@ def _served_jobs(seed, secs):
         t += rng.exponential(1.0 / SERVED["rate"])
         if t > secs:
             break
-        n = int(np.clip(rng.lognormal(np.log(SERVED["median"]), SERVED["sigma"]), SERVED["lo"], SERVED["hi"]))
-        L = int(rng.integers(100, 151))
+        ascii, offs = pool[int(rng.integers(len(pool)))]
         k = int(rng.choice(SERVED["ks"]))
-        ascii, offs = synth.uniform_genome_reads(int(rng.integers(1 << 30)), max(5000, n * L // 20), n, L, 0.005)
         j = serve.Job(ascii, offs, k, 2, tag=len(jobs))
         j.arrival = t
         jobs.append(j)
@@ -550,12 +566,13 @@ def run_served(args, rank, local):
         return
     torch.cuda.set_device(local)
     runner = serve.GpuRunner(local, SERVED["slots"])
-    warm = _served_jobs(SERVED["seed"] + 100, 0.5)
+    pool = _served_pool(SERVED["seed"])
+    warm = _served_jobs(pool, SERVED["seed"] + 100, 0.5)
     for _ in range(max(1, args.warmup)):
         for j in warm:
             j.__init__(j.ascii, j.offs, j.k, j.d, j.tag)
         _run_stream(warm, SERVED["slots"], SERVED["budget"], runner, False)
-    jobs = _served_jobs(SERVED["seed"], SERVED["secs"])
+    jobs = _served_jobs(pool, SERVED["seed"], SERVED["secs"])
     for c in runner.ctxs:
         c.profile_reset()
         c.set_profile(True)
