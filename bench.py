@@ -883,6 +883,9 @@ def main():
                        "l2": "inputs larger than L2 (%.1f GB of reads, %.1f GB of keys per step)"
                              % (n_bases / 1e9, info["n_kmers"] * 4 / 1e9)},
             "sdbg_edges_per_s": tot["edges"] * args.steps / (ms / 1e3),
+            # per call, device-timed: (k+1)-mers over mh_count_kmers, entries over mh_build_sdbg
+            "count_kmers_per_s": n_kmers / (phase_ms["count"] / 1e3) if phase_ms["count"] else None,
+            "build_edges_per_s": info["m"] / (phase_ms["build"] / 1e3) if phase_ms["build"] else None,
             "phases_ms": phase_ms,
             "sizes": {key: int(v) for key, v in info.items() if key not in ("buckets", "peak_GB")},
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
