@@ -188,3 +188,29 @@ def test_sdbg_structure(run):
     # dummy nodes hold only dummy entries
     assert np.array_equal(np.add.reduceat(dummy.astype(np.int64), starts) > 0, node_dummy)
     assert np.all(np.add.reduceat(dummy.astype(np.int64), starts)[node_dummy] == (ends - starts + 1)[node_dummy])
+
+
+def test_bucketed_count_matches_in_memory_count(run):
+    """Under a 70 GB budget the same workload is counted in buckets of the
+    mixed keys' top bits (reads resident, keys split); its solid and mercy
+    tables must equal the in-memory ones exactly."""
+    import torch
+
+    import paper_1409_7208_gb300 as mh
+
+    ctx = mh.Context(device=0, hbm_budget=70 << 30)
+    d_ascii = torch.from_numpy(run["ascii"]).cuda()
+    d_offs = torch.from_numpy(run["offs"].view(np.int64)).cuda()
+    reads = mh.mh_pack_reads(ctx, d_ascii, d_offs)
+    del d_ascii
+    ctx.set_profile(True)
+    solid = mh.mh_count_kmers(ctx, reads, K, D)
+    ctx.set_profile(False)
+    assert ctx.profile().get("extract_bucket", (0, 0, 0))[0] >= 2, "the budget should force buckets"
+    mercy = mh.mh_mercy_kmers(ctx, reads, solid)
+    s, m = solid.numpy(), mercy.numpy()
+    assert s["n_kmers"] == run["solid"]["n_kmers"] and s["n_distinct"] == run["solid"]["n_distinct"]
+    assert np.array_equal(s["keys"], run["solid"]["keys"]) and np.array_equal(s["counts"], run["solid"]["counts"])
+    assert np.array_equal(m["keys"], run["mercy"]["keys"]) and np.array_equal(m["counts"], run["mercy"]["counts"])
+    del mercy, solid, reads
+    ctx.close()
