@@ -341,7 +341,6 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
     uint32_t* wsum = wpre + kWords + 8;                                        // [8]
     uint16_t* hp = reinterpret_cast<uint16_t*>(wsum + 8);                      // [TILE] head positions
     uint64_t* out_stage_k = reinterpret_cast<uint64_t*>(hp + kRunTile);        // [TILE] if NW == 1
-    uint32_t* out_stage_c = reinterpret_cast<uint32_t*>(out_stage_k + (NW == 1 ? kRunTile : 0));  // [TILE]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t tile = blockIdx.x;
     const uint64_t start = tile * kRunTile;
@@ -469,8 +468,9 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
         for (uint32_t o = 0; o < nout[j]; o++) {
             const Key<NW> y = o == 0 ? xk : key_rc<NW>(xk, K1);
             if (staged) {
+                // keys staged for a coalesced write-out; counts go straight out
                 out_stage_k[lpos] = y.w[0];
-                out_stage_c[lpos] = cnt[j];
+                out_cnt[toff + lpos] = cnt[j];
                 lpos++;
             } else {
                 store_key<NW>(out_keys, pos, y);
@@ -481,10 +481,7 @@ __global__ void __launch_bounds__(kRunThreads) runs_kernel(const uint64_t* __res
     }
     if (staged) {
         __syncthreads();
-        for (uint32_t i = tid; i < n_out; i += kRunThreads) {
-            out_keys[toff + i] = out_stage_k[i];
-            out_cnt[toff + i] = out_stage_c[i];
-        }
+        for (uint32_t i = tid; i < n_out; i += kRunThreads) out_keys[toff + i] = out_stage_k[i];
     }
 }
 
@@ -582,7 +579,7 @@ void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, 
                   next.p);
         const size_t smem = sizeof(uint64_t) * kRunTilePad * NW + sizeof(uint32_t) * (2 * (kRunTile / 32) + 16) +
                             sizeof(uint16_t) * kRunTile +
-                            (NW == 1 ? (sizeof(uint64_t) + sizeof(uint32_t)) * kRunTile : 0);
+                            (NW == 1 ? sizeof(uint64_t) * kRunTile : 0);
         auto kern = in_mixed ? runs_kernel<NW, true> : runs_kernel<NW, false>;
         MH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         Buf<uint2> tstats(ctx, tiles);
