@@ -565,7 +565,7 @@ def run_served(args, rank, local):
     if rank != 0:
         return
     torch.cuda.set_device(local)
-    runner = serve.GpuRunner(local, SERVED["slots"])
+    runner = serve.DeviceRunner(local, SERVED["slots"])
     pool = _served_pool(SERVED["seed"])
     warm = _served_jobs(pool, SERVED["seed"] + 100, 0.5)
     for _ in range(max(1, args.warmup)):

@@ -71,7 +71,7 @@ class Server:
         self.slots = slots
         self.budget = hbm_budget
         self.auto_release = auto_release
-        self.runner = runner if runner is not None else GpuRunner(device, slots)
+        self.runner = runner if runner is not None else DeviceRunner(device, slots)
         self._q = collections.deque()
         self._cv = threading.Condition()
         self._held = 0          # bytes of admitted, unreleased jobs
@@ -136,7 +136,7 @@ class Server:
             t.join()
 
 
-class GpuRunner:
+class DeviceRunner:
     """One library context and one CUDA stream per slot.  The contexts use
     the library's own stream-ordered pools (no Python in the allocation
     path, so the slots' host threads do not contend for the interpreter);
