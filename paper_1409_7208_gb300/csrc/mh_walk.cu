@@ -16,11 +16,11 @@
 //            appends the label of out-edge r(w, j) mod (their number); it
 //            also stops at max_len symbols.
 //
-// A thread runs one walk: each step is one lower-bound search per table
-// (node.A) and a look at the next 4 entries.  The search starts from a
-// bucket index of each table over the top bits of its keys (about 16 keys a
-// bucket), so a step costs a few dependent loads instead of a search of the
-// whole table.  Walks write into fixed slots of max_len bytes, compacted
+// A warp runs one walk: each step finds, in each table, the entries whose
+// k-prefix is the node (node.A .. node.T) from a bucket index over the top
+// bits of the keys (about 16 keys a bucket): the lanes read the bucket in one
+// load and a ballot gives the first entry >= node.A, so a step costs a few
+// dependent loads.  Walks write into fixed slots of max_len bytes, compacted
 // afterwards.
 #include <algorithm>
 
@@ -56,45 +56,78 @@ __global__ void table_index_kernel(const uint64_t* __restrict__ T, uint64_t n, i
     }
 }
 
-// Labels (bit c for label c) of the entries of a sorted table with k-prefix v.
+// Labels (bit c for label c) of the out-edges of node v in both tables at
+// once: half-warp 0 searches the solid table, half-warp 1 the mercy table.
+// A half reads v.A's bucket 16 entries at a time and finds the first entry
+// >= v.A by a ballot (the bucket's end if none); its lanes 0..3 then read the
+// entries from there (into the next bucket when the index covers the label's
+// bits, for tiny k).  Every lane gets the union of both masks.
 template <int NW>
-__device__ __forceinline__ uint32_t out_labels(const uint64_t* __restrict__ T, uint64_t n,
-                                               const uint64_t* __restrict__ off, int K1, int bits,
-                                               const Key<NW>& v) {
-    if (!n) return 0;
+__device__ __forceinline__ uint32_t out_labels(const uint64_t* __restrict__ S, uint64_t nS,
+                                               const uint64_t* __restrict__ offS, const uint64_t* __restrict__ M,
+                                               uint64_t nM, const uint64_t* __restrict__ offM, int K1, int bits,
+                                               const Key<NW>& v, int lane) {
+    const int half = lane >> 4, hl = lane & 15;
+    const uint64_t* T = half ? M : S;
+    const uint64_t n = half ? nM : nS;
+    const uint64_t* off = half ? offM : offS;
     const Key<NW> q = key_shl<NW>(v, 2);
-    const uint64_t b = top_bits<NW>(q, K1, bits);
-    uint64_t lo = off[b], hi = off[b + 1];
-    while (lo < hi) {
-        const uint64_t mid = (lo + hi) >> 1;
-        if (key_less<NW>(load_key<NW>(T, mid), q)) lo = mid + 1; else hi = mid;
+    uint64_t lo = 0, hi = 0;
+    if (n) {
+        const uint64_t b = top_bits<NW>(q, K1, bits);
+        lo = off[b];
+        hi = off[b + 1];
     }
-    uint32_t mask = 0;
-    for (uint64_t i = lo; i < lo + 4 && i < n; i++) {
-        const Key<NW> e = load_key<NW>(T, i);
-        if (!key_eq<NW>(key_shr<NW>(e, 2), v)) break;
-        mask |= 1u << (uint32_t)(e.w[0] & 3u);
+    uint64_t pos = hi, base = lo;
+    bool done = base >= hi;
+    while (__ballot_sync(0xFFFFFFFFu, !done)) {
+        const uint64_t i = base + hl;
+        const bool ge = !done && i < hi && !key_less<NW>(load_key<NW>(T, i), q);
+        const uint32_t m = (__ballot_sync(0xFFFFFFFFu, ge) >> (16 * half)) & 0xFFFFu;
+        if (!done) {
+            if (m) {
+                pos = base + __ffs(m) - 1;
+                done = true;
+            } else {
+                base += 16;
+                done = base >= hi;
+            }
+        }
     }
+    bool hit = false;
+    uint32_t label = 0;
+    if (hl < 4 && pos + hl < n) {
+        const Key<NW> e = load_key<NW>(T, pos + hl);
+        hit = key_eq<NW>(key_shr<NW>(e, 2), v);
+        label = (uint32_t)(e.w[0] & 3u);
+    }
+    // entries of prefix v are consecutive from pos: lane l counts if lanes 0..l of its half all match
+    const uint32_t hm = (__ballot_sync(0xFFFFFFFFu, hit) >> (16 * half)) & 0xFu;
+    const uint32_t run = __ffs(~hm) - 1;  // matching entries from pos (at most 4)
+    uint32_t mask = (hl < (int)run) ? (1u << label) : 0u;
+    for (int o = 16; o; o >>= 1) mask |= __shfl_xor_sync(0xFFFFFFFFu, mask, o);
     return mask;
 }
 
+// One warp per walk (the searches of a step are warp-wide).
 template <int NW>
 __global__ void walk_kernel(const uint64_t* __restrict__ S, uint64_t nS, const uint64_t* __restrict__ offS,
                             const uint64_t* __restrict__ M, uint64_t nM, const uint64_t* __restrict__ offM,
                             int bits, int k, uint64_t n_walks, uint32_t max_len, uint64_t seed,
                             uint8_t* __restrict__ slots, uint64_t* __restrict__ lens) {
     const int K1 = k + 1;
+    const int lane = threadIdx.x & 31;
     const uint64_t E = nS + nM;
-    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < n_walks;
-         w += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; w < n_walks; w += n_warps) {
         uint8_t* out = slots + w * max_len;
         const uint64_t s = splitmix64_at(seed, w << 24) % E;
         Key<NW> x = s < nS ? load_key<NW>(S, s) : load_key<NW>(M, s - nS);
-        for (int i = 0; i < K1; i++) out[i] = "ACGT"[key_sym<NW>(x, K1, i)];
+        for (int i = lane; i < K1; i += 32) out[i] = "ACGT"[key_sym<NW>(x, K1, i)];
         uint32_t len = K1;
         for (uint32_t j = 1; len < max_len; j++) {
             const Key<NW> v = key_low<NW>(x, 2 * k);
-            const uint32_t mask = out_labels<NW>(S, nS, offS, K1, bits, v) | out_labels<NW>(M, nM, offM, K1, bits, v);
+            const uint32_t mask = out_labels<NW>(S, nS, offS, M, nM, offM, K1, bits, v, lane);
             if (!mask) break;
             uint32_t r = (uint32_t)(splitmix64_at(seed, (w << 24) + j) % (uint64_t)__popc(mask));
             uint32_t m = mask;
@@ -102,9 +135,10 @@ __global__ void walk_kernel(const uint64_t* __restrict__ S, uint64_t nS, const u
             const uint32_t c = __ffs(m) - 1;
             x = key_shl<NW>(v, 2);
             x.w[0] |= c;
-            out[len++] = "ACGT"[c];
+            if (lane == 0) out[len] = "ACGT"[c];
+            len++;
         }
-        lens[w] = len;
+        if (lane == 0) lens[w] = len;
     }
 }
 
@@ -137,7 +171,7 @@ void walk_contigs(mh_ctx* ctx, const mh_kmers* solid, const mh_kmers* mercy, uin
         if (nM)
             MH_LAUNCH(ctx, "walk_index", grid_for(ctx, nM, 256), 256, 0, table_index_kernel<NW>, mercy->keys, nM,
                       k + 1, bits, offM.p);
-        MH_LAUNCH(ctx, "walk", grid_for(ctx, n_walks, 128), 128, 0, walk_kernel<NW>, solid->keys, nS, offS.p,
+        MH_LAUNCH(ctx, "walk", grid_for(ctx, n_walks * 32, 256, 8), 256, 0, walk_kernel<NW>, solid->keys, nS, offS.p,
                   mercy ? mercy->keys : nullptr, nM, offM.p, bits, k, n_walks, max_len, seed, slots.p, lens.p);
     }
     exclusive_scan_u64(ctx, lens.p, off.p, n_walks);
