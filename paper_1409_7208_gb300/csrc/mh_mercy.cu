@@ -21,11 +21,11 @@
 //            position and the end of its fragment).
 //   walk     thread per hit: step forward to the next solid window q; if
 //            q > p+1 and q has no indegree, the windows p+1..q-1 are emitted
-//            (canonical keys).  Solidity of 1-word keys: a search of the
-//            counting spectrum (distinct canonical keys, ascending as mix_bij
-//            images, so evenly spread, with their run lengths) through a
-//            bucket index on their top bits; wider keys: a hash set of the
-//            canonical solid keys.
+//            (canonical keys).  Solidity: a search of the counting spectrum
+//            (distinct canonical keys, ascending as mix_key images, so their
+//            top bits are evenly spread, with their run lengths) through a
+//            bucket index on the top bits of the top word; handles without a
+//            mixed spectrum: a hash set of the canonical solid keys.
 //   finish   sort + dedup of the candidates, counts looked up in the
 //            counting spectrum, both strands, sorted.
 #include "mh_internal.cuh"
@@ -254,16 +254,17 @@ __device__ __forceinline__ uint32_t ends_find(const Slot<NW>* __restrict__ table
 // holding the key itself, empty = all ones (never canonical: the reverse
 // complement of T...T is A...A, which is smaller); wider keys use Slot
 // (32-bit tag + key).
-// Bucket index over the ascending mixed spectrum keys (1-word): off[b] =
-// first index whose top `bits` bits are >= b, for b = 0..2^bits (thread per
-// key; each bucket boundary is written by exactly one thread).
+// Bucket index over the ascending mixed spectrum keys: off[b] = first index
+// whose top `bits` bits (of the top word) are >= b, for b = 0..2^bits
+// (thread per key; each bucket boundary is written by exactly one thread).
+template <int NW>
 __global__ void canon_index_kernel(const uint64_t* __restrict__ canon, uint64_t n, int bits,
                                    uint64_t* __restrict__ off) {
     const int sh = 64 - bits;
     const uint64_t nb = 1ull << bits;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t b = canon[i] >> sh;
-        const uint64_t b0 = i == 0 ? 0 : (canon[i - 1] >> sh) + 1;
+        const uint64_t b = canon[i * NW + NW - 1] >> sh;
+        const uint64_t b0 = i == 0 ? 0 : (canon[(i - 1) * NW + NW - 1] >> sh) + 1;
         for (uint64_t x = b0; x <= b; x++) off[x] = i;
         if (i == n - 1)
             for (uint64_t x = b + 1; x <= nb; x++) off[x] = n;
@@ -271,15 +272,16 @@ __global__ void canon_index_kernel(const uint64_t* __restrict__ canon, uint64_t 
 }
 
 // Run length of the mixed key m in the ascending spectrum (bucket index
-// off over `bits` top bits), 0 if absent.
+// off over `bits` top bits of the top word), 0 if absent.
+template <int NW>
 __device__ __forceinline__ uint32_t spec_find(const uint64_t* __restrict__ spec, const uint32_t* __restrict__ len,
-                                              const uint64_t* __restrict__ off, int bits, uint64_t m) {
-    const uint64_t b = m >> (64 - bits);
+                                              const uint64_t* __restrict__ off, int bits, const Key<NW>& m) {
+    const uint64_t b = m.w[NW - 1] >> (64 - bits);
     uint64_t i = off[b];
     const uint64_t e = off[b + 1];
     for (; i < e; i++) {
-        const uint64_t v = spec[i];
-        if (v >= m) return v == m ? len[i] : 0u;
+        const Key<NW> v = load_key<NW>(spec, i);
+        if (!key_less<NW>(v, m)) return key_eq<NW>(v, m) ? len[i] : 0u;
     }
     return 0u;
 }
@@ -393,8 +395,8 @@ __global__ void __launch_bounds__(256) mercy_walk_kernel(const uint32_t* __restr
             Key<NW> r = key_rc<NW>(x, K1);
             const Key<NW> c = key_less<NW>(r, x) ? r : x;
             bool present;
-            if constexpr (MIXED && NW == 1) {
-                const uint32_t len = spec_find(spec, spec_len, spec_off, spec_bits, mix_bij(c.w[0]));
+            if constexpr (MIXED) {
+                const uint32_t len = spec_find<NW>(spec, spec_len, spec_off, spec_bits, mix_key<NW>(c));
                 present = (uint64_t)len * (key_eq<NW>(r, x) ? 2 : 1) >= (uint64_t)d;
             } else
                 present = table_has<NW>(solid, solid_mask, c);
@@ -454,21 +456,21 @@ void mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_k
         MH_LAUNCH(ctx, "mercy_ends_insert", grid_for(ctx, S, 256), 256, 0, ends_insert_kernel<NW>, solid->keys, S,
                   flags.p, table.p, cap - 1, filter.p, fbits / 32 - 1, ctx->d_status);
     flags.reset();
-    // solidity: 1-word keys use the counting handle's ascending mixed solid
-    // keys with a bucket index (4 to 8 keys a bucket); wider keys a hash set
-    // of the canonical solid keys, load <= 1/2 (<= 0.61 if all palindromes)
+    // solidity: the counting handle's ascending mixed spectrum with a bucket
+    // index (4 to 8 keys a bucket); without one, a hash set of the canonical
+    // solid keys, load <= 1/2 (<= 0.61 if all palindromes)
     const bool mixed = solid->spectrum_mixed;
     Buf<Slot<NW>> sset;
     uint64_t scap = 1;
     Buf<uint64_t> spec_off;
     int spec_bits = 1;
-    if (NW == 1 && mixed) {
+    if (mixed) {
         while (spec_bits < 40 && (2ull << spec_bits) * 4 <= solid->n_spectrum) spec_bits++;
         spec_off = Buf<uint64_t>(ctx, (1ull << spec_bits) + 1);
         spec_off.zero();
         if (solid->n_spectrum)
             MH_LAUNCH(ctx, "mercy_spectrum_index", grid_for(ctx, solid->n_spectrum, 256), 256, 0,
-                      canon_index_kernel, solid->spectrum, solid->n_spectrum, spec_bits, spec_off.p);
+                      canon_index_kernel<NW>, solid->spectrum, solid->n_spectrum, spec_bits, spec_off.p);
     } else {
         scap = next_pow2(std::max<uint64_t>(S + S / 2, 64));
         sset = Buf<Slot<NW>>(ctx, scap);
