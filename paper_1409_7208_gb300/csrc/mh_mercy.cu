@@ -188,12 +188,21 @@ __global__ void degree_flags_kernel(const uint8_t* __restrict__ fout, uint8_t* _
 }
 
 // Prefilter of the edges without outdegree: a blocked Bloom filter, three
-// bits of one 32-bit word per key (word from the hash's high bits, bit
-// positions from three 5-bit fields of its low bits), so a query is one
-// load; about 5% false positives at 8 bits per key.
-__device__ __forceinline__ uint64_t filter_word(uint64_t h, uint64_t words_mask) { return (h >> 20) & words_mask; }
+// bits of one 32-bit word per key, so a query is one load; about 5% false
+// positives at 8 bits per key.  Its hash is one multiply per key word (the
+// filter is probed for every read window; the table keeps key_hash): the
+// word comes from the product's top 32 bits, the bit positions from three
+// 5-bit fields of its middle bits.
+template <int NW>
+__device__ __forceinline__ uint64_t filter_hash(const Key<NW>& x) {
+    uint64_t h = x.w[0] * 0x9E3779B97F4A7C15ull;
+#pragma unroll
+    for (int w = 1; w < NW; w++) h ^= (x.w[w] + h) * 0xBF58476D1CE4E5B9ull;
+    return h;
+}
+__device__ __forceinline__ uint64_t filter_word(uint64_t h, uint64_t words_mask) { return (h >> 32) & words_mask; }
 __device__ __forceinline__ uint32_t filter_bits(uint64_t h) {
-    return (1u << (h & 31)) | (1u << ((h >> 5) & 31)) | (1u << ((h >> 10) & 31));
+    return (1u << ((h >> 17) & 31)) | (1u << ((h >> 22) & 31)) | (1u << ((h >> 27) & 31));
 }
 
 // Dead-end edges (oriented) with their flags into the small table; edges
@@ -210,7 +219,8 @@ __global__ void __launch_bounds__(256) ends_insert_kernel(const uint64_t* __rest
         Key<NW> x = load_key<NW>(S, i);
         uint64_t h = key_hash<NW>(x);
         if (f & 1u) {
-            atomicOr(&filter[filter_word(h, filter_mask)], filter_bits(h));
+            const uint64_t fh = filter_hash<NW>(x);
+            atomicOr(&filter[filter_word(fh, filter_mask)], filter_bits(fh));
         }
         uint32_t tag = slot_tag(h);
         uint64_t s = h & cap_mask;
@@ -350,7 +360,7 @@ __global__ void __launch_bounds__(256) mercy_probe_kernel(const uint32_t* __rest
             bool hit = false;
             if (p < nwin) {
                 const Key<NW> x = load_window<NW>(packed, b + p, K1);
-                const uint64_t h = key_hash<NW>(x);
+                const uint64_t h = filter_hash<NW>(x);
                 const uint32_t fm = filter_bits(h);
                 if ((__ldg(&filter[filter_word(h, filter_mask)]) & fm) == fm)
                     hit = (ends_find<NW>(ends, cap_mask, x) & 1u) != 0;
