@@ -101,3 +101,18 @@ def test_oversized_job_runs_alone():
     srv.close()
     assert big.start_t >= small[0].end_t, "runs when nothing else is held"
     assert small[1].start_t >= big.end_t, "FIFO behind the big job"
+
+
+def test_batch_read_counts_follow_the_batched_config():
+    """64 read counts: lognormal around a median of 500k (the geometric mean
+    of the bounds), clipped to [50k, 5M], even (pairs), reproducible."""
+    import numpy as np
+
+    import synth
+    c = synth.batch_read_counts(5, 64)
+    assert len(c) == 64 and np.array_equal(c, synth.batch_read_counts(5, 64))
+    assert c.min() >= 50_000 - 1 and c.max() <= 5_000_000 and np.all(c % 2 == 0)
+    big = synth.batch_read_counts(11, 20_000)
+    assert 0.8 * 500_000 < np.median(big) < 1.2 * 500_000
+    # sigma is a quarter of ln(5M / 50k): about 2.3% of the mass beyond each bound
+    assert 0.01 < np.mean(big >= 5_000_000) < 0.04 and 0.01 < np.mean(big <= 50_000) < 0.04
