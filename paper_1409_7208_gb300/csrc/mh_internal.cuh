@@ -534,21 +534,15 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
 }
-// Invertible 64-bit mixer: odd multipliers and a 32-bit xorshift are each
-// bijections of 64-bit words, so mix_bij permutes the keys (equal keys stay
-// equal, distinct keys stay distinct) while spreading their top bits.
-constexpr uint64_t kMixC1 = 0x9E3779B97F4A7C15ull, kMixC2 = 0xBF58476D1CE4E5B9ull;
-constexpr uint64_t kMixC1Inv = 0xF1DE83E19937733Dull, kMixC2Inv = 0x96DE1B173F119089ull;  // inverses mod 2^64
-__host__ __device__ __forceinline__ uint64_t mix_bij(uint64_t x) {
-    x *= kMixC1;
-    x ^= x >> 32;
-    return x * kMixC2;
-}
-__host__ __device__ __forceinline__ uint64_t unmix_bij(uint64_t h) {
-    h *= kMixC2Inv;
-    h ^= h >> 32;
-    return h * kMixC1Inv;
-}
+// Invertible 64-bit mixer: multiplication by an odd constant is a bijection
+// of 64-bit words, so mix_bij permutes the keys (equal keys stay equal,
+// distinct keys stay distinct), and every bit of the key reaches the top
+// bits of the product, which is all the sorts use (Fibonacci hashing: keys
+// that differ in a few symbols differ in their top bits).
+constexpr uint64_t kMixC1 = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t kMixC1Inv = 0xF1DE83E19937733Dull;  // its inverse mod 2^64
+__host__ __device__ __forceinline__ uint64_t mix_bij(uint64_t x) { return x * kMixC1; }
+__host__ __device__ __forceinline__ uint64_t unmix_bij(uint64_t h) { return h * kMixC1Inv; }
 
 // Multiword keys: word i is mixed together with the mixed word below it, so
 // the top word depends on every word (its top bits spread evenly) and each
