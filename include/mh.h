@@ -293,8 +293,9 @@ int mh_sort_shape(const mh_ctx* ctx);
 /* Sort n keys (nw = 1, 2 or 4 words each, layout as above) ascending by their
  * low key_bits bits (1 <= key_bits <= 64 * nw; higher bits must be zero),
  * reading keys_in and writing keys_out (distinct device buffers of n * nw
- * words on the calling thread's current device), on `stream` (a
- * cudaStream_t; NULL = the legacy default stream).  The paper has no
+ * words on the calling thread's current device, 8-byte aligned for nw = 1 and
+ * 16-byte aligned for nw = 2 or 4), on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream).  The paper has no
  * counterpart: this is the library's radix sort, offered to callers that may
  * not allocate device memory at all - hosts that own the device's whole
  * memory budget, or code that must never enter the driver's allocator or
@@ -305,11 +306,14 @@ int mh_sort_shape(const mh_ctx* ctx);
  *   * limit: n * nw <= 2^21 words (16 MiB of keys); larger inputs return
  *     MH_EOVERFLOW and touch nothing;
  *   * the first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *     (cudaGetSymbolAddress; again after the device's context is recreated);
+ *     make that first call before any stream capture;
  *   * every call on a device shares the array and clears what must start at
  *     zero itself; calls that overlap on the GPU race and must be avoided;
- *   * the call waits for `stream` at the end to read a status word.
- * Errors: MH_EINVAL (nw, key_bits, NULL or identical buffers), MH_EOVERFLOW,
+ *   * every call with n >= 1 waits for `stream` before it returns (to read a
+ *     status word, or after the single copy when n = 1).
+ * Errors: MH_EINVAL (nw, key_bits, NULL, identical or misaligned buffers),
+ * MH_EOVERFLOW,
  * MH_ETIMEOUT (a bounded look-back wait ran out), MH_EDEVICE. */
 int mh_sort_keys_noalloc(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n, int nw, int key_bits,
                          void* stream);

@@ -538,9 +538,24 @@ def mh_sort_keys_noalloc(keys_in, keys_out, nw: int, key_bits: int, stream=None)
     race on that array."""
     import torch
     lib = load_library()
+    if int(nw) not in (1, 2, 4):
+        raise ValueError("nw must be 1, 2 or 4")
+    for name, t in (("keys_in", keys_in), ("keys_out", keys_out)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError("%s must be a CUDA tensor" % name)
+        if t.dtype != torch.int64:
+            raise ValueError("%s must be int64 (uint64 bits)" % name)
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+    if keys_in.device != keys_out.device or keys_in.device.index != torch.cuda.current_device():
+        raise ValueError("keys_in and keys_out must be on the current CUDA device")
+    if keys_in.numel() % int(nw):
+        raise ValueError("keys_in holds %d words, not a multiple of nw = %d" % (keys_in.numel(), nw))
+    if keys_out.numel() < keys_in.numel():
+        raise ValueError("keys_out holds fewer words than keys_in")
     if stream is None:
         stream = torch.cuda.current_stream()
-    n = keys_in.numel() // nw
+    n = keys_in.numel() // int(nw)
     rc = lib.mh_sort_keys_noalloc(keys_in.data_ptr(), keys_out.data_ptr(), n, int(nw), int(key_bits),
                                   stream.cuda_stream)
     if rc != MH_OK:

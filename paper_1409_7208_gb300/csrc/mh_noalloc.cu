@@ -18,8 +18,13 @@
 // several threads without ordering) race on the array and must not be made.
 //
 // In host code the array's name only stands for the device object; its
-// device address is looked up once per device with cudaGetSymbolAddress,
-// while that device is current, by the first call made on it.
+// device address is looked up with cudaGetSymbolAddress, while that device
+// is current, by the first call made on the device, and again only if the
+// device's primary context has been torn down and recreated since (a context
+// id is kept beside the address, so an address from a dead context is never
+// reused).
+#include <cuda.h>
+
 #include <mutex>
 
 #include "mh_sort_kernels.cuh"
@@ -53,9 +58,38 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 static std::mutex g_scratch_mu;
 static void* g_scratch_addr[kMaxDevices];
+static unsigned long long g_scratch_ctx[kMaxDevices];  // context id the address belongs to
 
-// Device address of the scratch array on the current device (looked up on
-// the first call per device).
+// Id of the current context (unique for the process's lifetime, unlike the
+// context handle), through the driver entry points cudart exposes; 0 if it
+// cannot be had.
+static unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        cudaGetLastError();
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the scratch array on the current device: looked up on
+// the first call per device, and again whenever the device's context is not
+// the one the cached address was taken in.
 static int scratch_address(void** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -63,14 +97,16 @@ static int scratch_address(void** out) {
         return MH_EDEVICE;
     }
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    unsigned long long ctx_id = current_context_id();  // 0 before the device's first runtime call
+    if (!g_scratch_addr[dev] || ctx_id == 0 || g_scratch_ctx[dev] != ctx_id) {
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // also makes the context current
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
             return MH_EDEVICE;
         }
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = current_context_id();
     }
     *out = g_scratch_addr[dev];
     return MH_OK;
@@ -134,11 +170,15 @@ extern "C" int mh_sort_keys_noalloc(const uint64_t* keys_in, uint64_t* keys_out,
     using namespace mh;
     if ((nw != 1 && nw != 2 && nw != 4) || key_bits < 1 || key_bits > 64 * nw) return MH_EINVAL;
     if (n > 0 && (!keys_in || !keys_out || keys_in == keys_out)) return MH_EINVAL;
+    // keys move as 8-byte words (one word) or 16-byte vectors (two or four)
+    const uintptr_t align = nw == 1 ? 7u : 15u;
+    if (n > 0 && (((uintptr_t)keys_in | (uintptr_t)keys_out) & align)) return MH_EINVAL;
     if (n > kMaxKeyWords / (uint64_t)nw) return MH_EOVERFLOW;
     if (n == 0) return MH_OK;
     cudaStream_t st = (cudaStream_t)stream;
     if (n == 1) {
-        if (cudaMemcpyAsync(keys_out, keys_in, 8 * (size_t)nw, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+        if (cudaMemcpyAsync(keys_out, keys_in, 8 * (size_t)nw, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
             cudaGetLastError();
             return MH_EDEVICE;
         }

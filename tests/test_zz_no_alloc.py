@@ -13,14 +13,13 @@ import ctypes
 import numpy as np
 import pytest
 
-pytestmark = pytest.mark.gpu
-
 
 def _call(lib, src, dst, n, nw, key_bits, stream):
     return lib.mh_sort_keys_noalloc(ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()), n, nw,
                                     key_bits, ctypes.c_void_p(stream.cuda_stream))
 
 
+@pytest.mark.gpu
 def test_noalloc_sort_matches_count_kmers_on_consecutive_calls():
     import torch
 
@@ -30,7 +29,8 @@ def test_noalloc_sort_matches_count_kmers_on_consecutive_calls():
     lib = mh.load_library()
     ctx = mh.Context(device=0)
     stream = torch.cuda.current_stream()
-    for call, (k, seed) in enumerate(((21, 41), (47, 42), (31, 43))):
+    # one-, two-, four- and one-word keys again: every call reuses the array
+    for call, (k, seed) in enumerate(((21, 41), (47, 42), (99, 44), (31, 43))):
         ascii, offs = synth.uniform_genome_reads(seed, 4000, 900, 130, 0.01)
         reads = mh.mh_pack_reads(ctx, ascii, offs)
         solid = mh.mh_count_kmers(ctx, reads, k, 2)
@@ -47,6 +47,44 @@ def test_noalloc_sort_matches_count_kmers_on_consecutive_calls():
         assert torch.equal(out, want), "call %d differs from mh_count_kmers" % call
 
 
+@pytest.mark.gpu
+def test_noalloc_sort_wide_keys_with_ragged_key_bits():
+    """Four-word keys sorted by 200 bits (not a whole number of digits), twice
+    in a row, against a lexicographic sort of the words on the host."""
+    import torch
+
+    import paper_1409_7208_gb300 as mh
+
+    rng = np.random.default_rng(7)
+    n = 9000
+    for call in range(2):
+        words = rng.integers(0, 1 << 63, size=(n, 4), dtype=np.int64).astype(np.uint64)
+        words[:, 3] &= np.uint64((1 << 8) - 1)  # 200 bits: 3 full words + 8 bits
+        words[: n // 3] = words[n // 3: 2 * (n // 3)]  # duplicates
+        order = np.lexsort((words[:, 0], words[:, 1], words[:, 2], words[:, 3]))
+        want = words[order]
+        src = torch.from_numpy(words.view(np.int64)).cuda()
+        dst = torch.full_like(src, -1)
+        mh.mh_sort_keys_noalloc(src, dst, 4, 200)
+        torch.cuda.synchronize()
+        assert np.array_equal(dst.cpu().numpy().view(np.uint64), want), "call %d" % call
+
+
+def test_noalloc_sort_rejects_misaligned_buffers_before_touching_the_device():
+    """The argument checks come before any CUDA call, so this runs without a
+    GPU: the addresses are never dereferenced."""
+    import paper_1409_7208_gb300 as mh
+
+    lib = mh.load_library()
+    a, b = 0x10000, 0x20000
+    for nw in (2, 4):
+        assert lib.mh_sort_keys_noalloc(ctypes.c_void_p(a + 8), ctypes.c_void_p(b), 10, nw, 64, None) == mh.MH_EINVAL
+        assert lib.mh_sort_keys_noalloc(ctypes.c_void_p(a), ctypes.c_void_p(b + 8), 10, nw, 64, None) == mh.MH_EINVAL
+    assert lib.mh_sort_keys_noalloc(ctypes.c_void_p(a + 4), ctypes.c_void_p(b), 10, 1, 64, None) == mh.MH_EINVAL
+    assert lib.mh_sort_keys_noalloc(ctypes.c_void_p(a), ctypes.c_void_p(b), 0, 2, 64, None) == mh.MH_OK
+
+
+@pytest.mark.gpu
 def test_noalloc_sort_rejects_oversize_and_bad_arguments():
     import torch
 
