@@ -33,20 +33,22 @@ __global__ void frag_windows_kernel(const uint64_t* __restrict__ frag_offs, uint
 }
 
 // Warp per fragment: canonical key of every window, written at woff[f] + i
-// (MIXED: its mix_bij image, 1-word keys).  With `hist`, the block also
-// counts the digits the sort's passes will use (n_passes digits of 8 bits
-// from bit shift0; in dynamic shared memory, added to hist at the end), so
-// the sort needs no histogram pass of its own.
+// (MIXED: its mix_bij image, 1-word keys).  With `hist` (1-word keys), the
+// block also counts the digits the sort's passes will use (n_passes digits of
+// rb bits from bit shift0; in dynamic shared memory, added to hist at the
+// end), so the sort needs no histogram pass of its own.
 template <int NW, bool MIXED>
 __global__ void __launch_bounds__(256) extract_canonical_kernel(const uint32_t* __restrict__ packed,
                                                                 const uint64_t* __restrict__ frag_offs,
                                                                 const uint64_t* __restrict__ woff, uint64_t n_frags,
                                                                 int k, uint64_t* __restrict__ out,
                                                                 uint32_t* __restrict__ hist, int shift0,
-                                                                int n_passes) {
+                                                                int n_passes, int rb) {
     extern __shared__ uint32_t sh[];
+    const int nbins = n_passes << rb;
+    const uint32_t dmask = (1u << rb) - 1u;
     if (hist) {
-        for (int i = threadIdx.x; i < n_passes * 256; i += blockDim.x) sh[i] = 0;
+        for (int i = threadIdx.x; i < nbins; i += blockDim.x) sh[i] = 0;
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
@@ -75,8 +77,11 @@ __global__ void __launch_bounds__(256) extract_canonical_kernel(const uint32_t* 
             Key<NW> c = key_less<NW>(r, x) ? r : x;
             if constexpr (MIXED) c = mix_key<NW>(c);
             store_key<NW>(out, w0 + i, c);
-            if (hist)
-                for (int p = 0; p < n_passes; p++) atomicAdd(&sh[p * 256 + key_digit<NW>(c, shift0 + 8 * p)], 1u);
+            if constexpr (NW == 1) {
+                if (hist)
+                    for (int p = 0; p < n_passes; p++)
+                        atomicAdd(&sh[(p << rb) + ((uint32_t)(c.w[0] >> (shift0 + rb * p)) & dmask)], 1u);
+            }
         }
         b = nb;
         w0 = nw0;
@@ -84,7 +89,7 @@ __global__ void __launch_bounds__(256) extract_canonical_kernel(const uint32_t* 
     }
     if (hist) {
         __syncthreads();
-        for (int i = threadIdx.x; i < n_passes * 256; i += blockDim.x)
+        for (int i = threadIdx.x; i < nbins; i += blockDim.x)
             if (sh[i]) atomicAdd(&hist[i], sh[i]);
     }
 }
@@ -677,6 +682,17 @@ static int count_bucket_bits(mh_ctx* ctx, uint64_t n, int nw) {
     return bb;
 }
 
+// The unit counting (wide-digit passes, units sorted and counted on chip)
+// for 1-word keys, unless MH_COUNT_PATH=spread selects the 8-bit spread sort
+// with the fix-up and the run pass (A/B runs and tests).
+static bool use_unit_count() {
+    static const bool v = [] {
+        const char* e = std::getenv("MH_COUNT_PATH");
+        return !(e && std::string(e) == "spread");
+    }();
+    return v;
+}
+
 template <int NW>
 void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out) {
     const uint64_t F = reads->n_frags;
@@ -697,6 +713,39 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
     out->n_kmers = 2 * n;
     out->spectrum_mixed = kMixed;
     const int bb = count_bucket_bits(ctx, n, NW);
+    const GroupPlan gp = group_plan(n, 0);
+    if (bb == 0 && NW == 1 && use_unit_count() && gp.passes >= 0) {
+        // 1-word keys: 8-bit passes over the top bits, then the units sorted
+        // and counted by a warp each (mh_group.cu)
+        Buf<uint64_t> keys(ctx, n ? n : 1), alt(ctx, n ? n : 1);
+        const int G = 8 * gp.passes;
+        Buf<uint32_t> hist(ctx, gp.passes ? (size_t)gp.passes * 256 : 1);
+        if (gp.passes) hist.zero();
+        if (n)
+            MH_LAUNCH_B(ctx, "extract_canonical", reads->n_packed / 4 + n * 8, grid_for(ctx, F * 32, 256, 8), 256,
+                        gp.passes ? sizeof(uint32_t) * gp.passes * 256 : 0, (extract_canonical_kernel<NW, kMixed>),
+                        reads->packed, reads->frag_offs, woff.p, F, k, keys.p, gp.passes ? hist.p : nullptr, 64 - G,
+                        gp.passes, 8);
+        woff.reset();
+        const bool in_alt = G ? radix_sort<1>(ctx, keys.p, alt.p, nullptr, nullptr, n, 64 - G, 64, hist.p) : false;
+        hist.reset();
+        Buf<uint64_t>& sorted = in_alt ? alt : keys;
+        Buf<uint64_t>& other = in_alt ? keys : alt;
+        Buf<uint64_t> sk;
+        Buf<uint32_t> sc;
+        uint64_t S = 0, runs = 0, palins = 0;
+        RunList list;
+        group_count(ctx, sorted, other, n, k, d, 0, gp, sk, sc, &S, &runs, &palins, &list);
+        sync_and_check(ctx);
+        out->n = S;
+        out->n_distinct = 2 * runs - palins;
+        out->keys = sk.release();
+        out->counts = sc.release();
+        out->n_spectrum = list.n;
+        out->spectrum = list.keys.release();
+        out->spectrum_len = list.lens.release();
+        return;
+    }
     if (bb == 0) {
         Buf<uint64_t> keys(ctx, (n ? n : 1) * NW), alt(ctx, (n ? n : 1) * NW);
         // the extraction counts the digits of the spread sort's passes (1-word
@@ -710,7 +759,7 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
             MH_LAUNCH_B(ctx, "extract_canonical", reads->n_packed / 4 + n * 8 * NW, grid_for(ctx, F * 32, 256, 8),
                         256, fuse ? sizeof(uint32_t) * n_passes * 256 : 0, (extract_canonical_kernel<NW, kMixed>),
                         reads->packed, reads->frag_offs, woff.p, F, k, keys.p, fuse ? hist.p : nullptr,
-                        64 * NW - P, n_passes);
+                        64 * NW - P, n_passes, 8);
         woff.reset();
         bool in_alt = radix_sort_spread<NW>(ctx, keys.p, alt.p, n, 0, fuse ? hist.p : nullptr);
         hist.reset();
@@ -774,18 +823,30 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
                         extract_bucket_kernel<NW>, reads->packed, reads->frag_offs, woff.p, ids.p, F, k, b, n_tasks,
                         toff[b].p, keys.p);
         toff[b].reset();
-        const bool in_alt = radix_sort_spread<NW>(ctx, keys.p, alt.p, m, bb);
-        Buf<uint64_t>& sorted = in_alt ? alt : keys;
-        Buf<uint64_t>& other = in_alt ? keys : alt;
         Buf<uint64_t> sk;
         Buf<uint32_t> sc;
         uint64_t S = 0, runs = 0, palins = 0;
         RunList list;
-        list.slot = std::move(other);
-        other.reset();
-        expand_runs<NW>(ctx, sorted.p, m, k, d, sk, sc, &S, &runs, &palins, nullptr, nullptr, 0, kMixed, false,
-                        &list);
-        sorted.reset();
+        const GroupPlan bp = group_plan(m, bb);
+        if (NW == 1 && use_unit_count() && bp.passes >= 0) {
+            const bool in_alt = bp.passes ? radix_sort<1>(ctx, keys.p, alt.p, nullptr, nullptr, m,
+                                                          64 - bb - 8 * bp.passes, 64 - bb)
+                                          : false;
+            Buf<uint64_t>& sorted = in_alt ? alt : keys;
+            Buf<uint64_t>& other = in_alt ? keys : alt;
+            group_count(ctx, sorted, other, m, k, d, bb, bp, sk, sc, &S, &runs, &palins, &list);
+        } else {
+            const bool in_alt = radix_sort_spread<NW>(ctx, keys.p, alt.p, m, bb);
+            Buf<uint64_t>& sorted = in_alt ? alt : keys;
+            Buf<uint64_t>& other = in_alt ? keys : alt;
+            list.slot = std::move(other);
+            other.reset();
+            expand_runs<NW>(ctx, sorted.p, m, k, d, sk, sc, &S, &runs, &palins, nullptr, nullptr, 0, kMixed, false,
+                            &list);
+            sorted.reset();
+        }
+        keys.reset();
+        alt.reset();
         runs_tot += runs;
         palins_tot += palins;
         part_k.push_back(std::move(list.keys));

@@ -446,6 +446,38 @@ __device__ __forceinline__ uint64_t gallop_lb(const uint64_t* __restrict__ a, ui
     return lo;
 }
 
+// ------------------------------------------------------ bitmask scans
+// First set bit at or after i in b (bits [0, n)), or n.
+__device__ __forceinline__ uint32_t next_bit(const uint32_t* b, uint32_t i, uint32_t n) {
+    if (i >= n) return n;
+    uint32_t w = i >> 5;
+    uint32_t m = b[w] & ~((1u << (i & 31)) - 1u);
+    while (true) {
+        if (m) {
+            const uint32_t r = w * 32 + __ffs(m) - 1;
+            return r < n ? r : n;
+        }
+        if (++w * 32 >= n) return n;
+        m = b[w];
+    }
+}
+
+// Last set bit at or before i in b, or ~0u.
+__device__ __forceinline__ uint32_t prev_bit(const uint32_t* b, uint32_t i) {
+    int w = (int)(i >> 5);
+    uint32_t m = b[w] & (0xFFFFFFFFu >> (31 - (i & 31)));
+    while (true) {
+        if (m) return (uint32_t)w * 32 + 31 - __clz(m);
+        if (--w < 0) return ~0u;
+        m = b[w];
+    }
+}
+
+// Any set bit in [i, j)?
+__device__ __forceinline__ bool any_bit(const uint32_t* b, uint32_t i, uint32_t j) {
+    return next_bit(b, i, j) < j;
+}
+
 // ------------------------------------------------ tile compaction helpers
 // 64-bit per-tile status words for decoupled look-back: flag in the top two
 // bits (aggregate / inclusive), count in the low 62.
@@ -632,6 +664,27 @@ struct RunList {
     Buf<uint32_t> lens;
     uint64_t n = 0;
 };
+
+// How the unit counting splits n 1-word keys whose top `skip` bits are
+// equal: units of the next unit_bits bits (about 100-160 keys each), sorted
+// into place by `passes` 8-bit LSD passes over the next 8 * passes bits.
+// passes < 0: the keys are too narrow for it (the spread path is used).
+struct GroupPlan {
+    int unit_bits = 0;
+    int passes = 0;
+};
+GroupPlan group_plan(uint64_t n, int skip);
+
+// Unit counting of mixed canonical 1-word keys (defined in mh_group.cu):
+// `sorted` holds n keys sorted by their top skip + 8 * plan.passes bits,
+// `other` n free words.  Each unit is sorted on chip and run-length counted:
+// out_keys / out_cnt get the kept (k+1)-mers of both strands (count >= d,
+// ascending), list the spectrum (every run's mixed key and length,
+// ascending).  Both input buffers are consumed (freed).
+void group_count(mh_ctx* ctx, Buf<uint64_t>& sorted, Buf<uint64_t>& other, uint64_t n, int k, int d, int skip,
+                 const GroupPlan& plan, Buf<uint64_t>& out_keys, Buf<uint32_t>& out_cnt, uint64_t* n_out,
+                 uint64_t* n_runs, uint64_t* n_palin_runs, RunList* list);
+
 
 // Sorted canonical keys -> solid (k+1)-mers, both strands, sorted.  Defined
 // in mh_count.cu, used by mercy too (d = 1, counts looked up in the

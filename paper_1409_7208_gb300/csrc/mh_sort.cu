@@ -146,37 +146,6 @@ struct Fix {
 constexpr int kFixWarpRounds = 64;
 constexpr int kFixBlockRounds = 256;
 
-// First set bit at or after i in b (bits [0, n)), or n.
-__device__ __forceinline__ uint32_t next_bit(const uint32_t* b, uint32_t i, uint32_t n) {
-    if (i >= n) return n;
-    uint32_t w = i >> 5;
-    uint32_t m = b[w] & ~((1u << (i & 31)) - 1u);
-    while (true) {
-        if (m) {
-            const uint32_t r = w * 32 + __ffs(m) - 1;
-            return r < n ? r : n;
-        }
-        if (++w * 32 >= n) return n;
-        m = b[w];
-    }
-}
-
-// Last set bit at or before i in b, or ~0u.
-__device__ __forceinline__ uint32_t prev_bit(const uint32_t* b, uint32_t i) {
-    int w = (int)(i >> 5);
-    uint32_t m = b[w] & (0xFFFFFFFFu >> (31 - (i & 31)));
-    while (true) {
-        if (m) return (uint32_t)w * 32 + 31 - __clz(m);
-        if (--w < 0) return ~0u;
-        m = b[w];
-    }
-}
-
-// Any set bit in [i, j)?
-__device__ __forceinline__ bool any_bit(const uint32_t* b, uint32_t i, uint32_t j) {
-    return next_bit(b, i, j) < j;
-}
-
 template <int NW>
 __device__ __forceinline__ Key<NW> shfl_key(const Key<NW>& a, int src_lane_xor) {
     Key<NW> r;

@@ -247,3 +247,4 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
 }
 
 }  // namespace mh
+

@@ -9,7 +9,17 @@ the key-value form of the spread order for solid tables (thread, warp and
 segment sorts of groups), the out-of-core count (2 or 16 buckets of keys counted one at a time,
 spectra concatenated, solid tables merged), and reads streamed from host
 memory through staging pieces of 48 bytes or 4 KB (pieces that end inside a
-read, reads that span several pieces, invalid bytes found mid-stream)."""
+read, reads that span several pieces, invalid bytes found mid-stream).
+
+The unit counting of 1-word keys (8-bit passes over the top bits, then each
+unit sorted and counted by a warp) is forced through its rarer paths the
+same way: units too large for a warp's shared memory (counted from global
+memory one distinct key a round, or, with too many distinct keys, set aside,
+sorted by the general radix sort and counted from the sorted keys), one unit
+holding every key, many nearly empty units under three passes, and runs of
+one key thousands of windows long (a read repeated 7,000 times).  The spread
+path it replaced (passes over the top 32 bits, a fix-up, a run pass) stays
+selectable and is checked as well."""
 import os
 import subprocess
 import sys
@@ -39,8 +49,18 @@ for a, o in (synth.random_reads(5, 400, 0, 300), synth.random_reads(6, 300, 0, 2
     assert np.array_equal(r["packed"].cpu().numpy().view(np.uint32), words)
     assert np.array_equal(r["frag_offs"].cpu().numpy().view(np.uint64), fo)
     assert np.array_equal(r["frag_read"].cpu().numpy().view(np.uint32), fr)
-for seed, k, n_reads in ((1, 21, 3000), (2, 31, 2500), (3, 47, 1500), (4, 99, 900)):
-    ascii, offs = synth.uniform_genome_reads(seed, 4000, n_reads, 150, 0.01)
+def repeated(seed):
+    # one 40-base read 7,000 times among random reads: runs longer than a unit holds
+    a, o = synth.uniform_genome_reads(seed, 4000, 800, 150, 0.01)
+    rep = np.frombuffer(bytes(a[:40]), dtype=np.uint8)
+    ascii = np.concatenate([np.tile(rep, 7000), a])
+    offs = np.concatenate([np.arange(7000, dtype=np.uint64) * 40, o.astype(np.uint64) + 7000 * 40])
+    return ascii, offs
+for seed, k, n_reads in ((1, 21, 3000), (2, 31, 2500), (3, 47, 1500), (4, 99, 900), (5, 21, 0)):
+    if n_reads:
+        ascii, offs = synth.uniform_genome_reads(seed, 4000, n_reads, 150, 0.01)
+    else:
+        ascii, offs = repeated(seed)
     reads = mh.mh_pack_reads(ctx, ascii, offs)
     s = mh.mh_count_kmers(ctx, reads, k, 2)
     m = mh.mh_mercy_kmers(ctx, reads, s)
@@ -56,16 +76,20 @@ print("ok")
 """ % ROOT
 
 
-@pytest.mark.parametrize("var,val", [("MH_SORT_CHUNK_TILES", "1"), ("MH_SORT_CHUNK_TILES", "3"),
-                                     ("MH_SPREAD_BITS", "8"), ("MH_SPREAD_BITS", "16"),
-                                     ("MH_SPREAD_BITS", "24"), ("MH_COUNT_BUCKET_BITS", "1"),
-                                     ("MH_COUNT_BUCKET_BITS", "4"), ("MH_SPREAD_KV_MIN", "0"),
-                                     ("MH_PACK_PIECE", "48"),
-                                     ("MH_PACK_PIECE", "4096")])
-def test_small_input_paths_match_oracle(var, val):
+@pytest.mark.parametrize("env", [
+    {"MH_SORT_CHUNK_TILES": "1"}, {"MH_SORT_CHUNK_TILES": "3"},
+    {"MH_COUNT_PATH": "spread", "MH_SPREAD_BITS": "8"}, {"MH_COUNT_PATH": "spread", "MH_SPREAD_BITS": "16"},
+    {"MH_COUNT_PATH": "spread", "MH_SPREAD_BITS": "24"}, {"MH_COUNT_PATH": "spread"},
+    {"MH_GROUP_CAP": "16"}, {"MH_GROUP_CAP": "200"}, {"MH_GROUP_UNIT_BITS": "0"},
+    {"MH_GROUP_UNIT_BITS": "6", "MH_GROUP_CAP": "64"},
+    {"MH_GROUP_UNIT_BITS": "14"}, {"MH_GROUP_UNIT_BITS": "22", "MH_SORT_CHUNK_TILES": "3"},
+    {"MH_COUNT_BUCKET_BITS": "1"}, {"MH_COUNT_BUCKET_BITS": "4"},
+    {"MH_COUNT_BUCKET_BITS": "4", "MH_COUNT_PATH": "spread"}, {"MH_SPREAD_KV_MIN": "0"},
+    {"MH_PACK_PIECE": "48"}, {"MH_PACK_PIECE": "4096"}], ids=lambda e: ",".join("%s=%s" % kv for kv in e.items()))
+def test_small_input_paths_match_oracle(env):
     # every run also sorts the small solid tables by the spread key-value path
-    env = dict(os.environ, MH_SPREAD_KV_MIN="0")
-    env[var] = val
-    p = subprocess.run([sys.executable, "-c", CHILD], env=env, capture_output=True, text=True, timeout=600)
+    full = dict(os.environ, MH_SPREAD_KV_MIN="0")
+    full.update(env)
+    p = subprocess.run([sys.executable, "-c", CHILD], env=full, capture_output=True, text=True, timeout=900)
     assert p.returncode == 0, p.stdout + p.stderr
     assert "ok" in p.stdout
