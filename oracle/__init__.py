@@ -79,6 +79,9 @@ def _load():
             lib.orc_count_queries.restype = ctypes.c_int
             lib.orc_fragments.argtypes = [u8p, u64p, ctypes.c_uint64, ctypes.c_char_p, u64p, u32p]
             lib.orc_fragments.restype = ctypes.c_uint64
+            lib.orc_find_windows.argtypes = [u8p, u64p, ctypes.c_uint64, ctypes.c_int, u64p, ctypes.c_uint64,
+                                             ctypes.c_uint64, u64p, u64p, u64p, ctypes.c_int]
+            lib.orc_find_windows.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -207,6 +210,32 @@ def count_queries(ascii, offs, k: int, queries, n_threads: int | None = None) ->
     if rc != 0:
         raise ValueError("oracle count_queries failed")
     return out
+
+
+def find_windows(ascii, offs, k: int, queries, cap: int = 1 << 20, n_threads: int | None = None):
+    """Every occurrence of the query keys as a forward window of a fragment:
+    arrays (query index, read index, window position in the read), sorted,
+    at most ``cap`` of them (ValueError beyond)."""
+    lib = _load()
+    nw = words_for(k)
+    ascii = np.ascontiguousarray(ascii, dtype=np.uint8)
+    offs = np.ascontiguousarray(offs, dtype=np.uint64)
+    q = np.ascontiguousarray(np.asarray(queries, dtype=np.uint64).reshape(-1, nw))
+    hq = np.zeros(max(1, cap), dtype=np.uint64)
+    hr = np.zeros(max(1, cap), dtype=np.uint64)
+    hp = np.zeros(max(1, cap), dtype=np.uint64)
+    if n_threads is None:
+        n_threads = max(1, min(64, os.cpu_count() or 1))
+    a = ascii if len(ascii) else np.zeros(1, dtype=np.uint8)
+    qq = q if q.shape[0] else np.zeros((1, nw), dtype=np.uint64)
+    n = lib.orc_find_windows(_p(a, ctypes.c_uint8), _p(offs, ctypes.c_uint64), len(offs) - 1, k,
+                             _p(qq, ctypes.c_uint64), q.shape[0], cap, _p(hq, ctypes.c_uint64),
+                             _p(hr, ctypes.c_uint64), _p(hp, ctypes.c_uint64), n_threads)
+    if n < 0:
+        raise ValueError("oracle find_windows failed")
+    if n > cap:
+        raise ValueError("%d hits, more than the cap of %d" % (n, cap))
+    return hq[:n].copy(), hr[:n].copy(), hp[:n].copy()
 
 
 # ------------------------------------------------------------ key helpers

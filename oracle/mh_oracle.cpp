@@ -451,4 +451,71 @@ int orc_count_queries(const uint8_t* ascii, const uint64_t* offs, uint64_t n_rea
     return 0;
 }
 
+// Every occurrence of the query keys as a forward (k+1)-mer window of a
+// fragment (no invalid byte inside it): (query index, read index, position
+// of the window's first base in the read).  For tracing a (k+1)-mer back to
+// the reads that contain it (the mercy rule of Sec. 2, third paragraph, is a
+// statement about a read and its windows).  At most `cap` hits are stored,
+// sorted by (query, read, position); returns the number of hits found, or -1
+// on a bad argument.
+int64_t orc_find_windows(const uint8_t* ascii, const uint64_t* offs, uint64_t n_reads, int k,
+                         const uint64_t* queries, uint64_t n_queries, uint64_t cap, uint64_t* hit_q,
+                         uint64_t* hit_read, uint64_t* hit_pos, int n_threads) {
+    if (k < 2 || k > 127) return -1;
+    const int nw = words_for(k);
+    const int bits = 2 * (k + 1);
+    std::unordered_map<Wide, uint64_t, WideHash> index;
+    for (uint64_t q = 0; q < n_queries; q++) {
+        Wide x = {{0, 0, 0, 0}};
+        for (int w = 0; w < nw; w++) x.w[w] = queries[q * nw + w];
+        index[x] = q;
+    }
+    if (n_threads < 1) n_threads = 1;
+    struct Hit {
+        uint64_t q, r, p;
+    };
+    std::vector<std::vector<Hit>> part(n_threads);
+    auto work = [&](int t) {
+        uint64_t r0 = n_reads * t / n_threads, r1 = n_reads * (t + 1) / n_threads;
+        for (uint64_t r = r0; r < r1; r++) {
+            Wide fwd = {{0, 0, 0, 0}};
+            int run = 0;
+            for (uint64_t j = offs[r]; j < offs[r + 1]; j++) {
+                char ch = (char)ascii[j];
+                if (ch >= 'a' && ch <= 'z') ch = (char)(ch - 'a' + 'A');
+                int c = code_of(ch);
+                if (c < 0) { run = 0; continue; }
+                for (int w = 3; w > 0; w--) fwd.w[w] = (fwd.w[w] << 2) | (fwd.w[w - 1] >> 62);
+                fwd.w[0] = (fwd.w[0] << 2) | (uint64_t)c;
+                for (int w = 0; w < 4; w++) {
+                    int lo = 64 * w;
+                    if (bits <= lo) fwd.w[w] = 0;
+                    else if (bits < lo + 64) fwd.w[w] &= (1ull << (bits - lo)) - 1;
+                }
+                run++;
+                if (run >= k + 1) {
+                    auto it = index.find(fwd);
+                    if (it != index.end()) part[t].push_back({it->second, r, j - offs[r] - (uint64_t)k});
+                }
+            }
+        }
+    };
+    std::vector<std::thread> th;
+    for (int t = 0; t < n_threads; t++) th.emplace_back(work, t);
+    for (auto& x : th) x.join();
+    std::vector<Hit> all;
+    for (auto& v : part) all.insert(all.end(), v.begin(), v.end());
+    std::sort(all.begin(), all.end(), [](const Hit& a, const Hit& b) {
+        if (a.q != b.q) return a.q < b.q;
+        if (a.r != b.r) return a.r < b.r;
+        return a.p < b.p;
+    });
+    for (uint64_t i = 0; i < all.size() && i < cap; i++) {
+        hit_q[i] = all[i].q;
+        hit_read[i] = all[i].r;
+        hit_pos[i] = all[i].p;
+    }
+    return (int64_t)all.size();
+}
+
 }  // extern "C"

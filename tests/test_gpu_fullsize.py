@@ -9,8 +9,12 @@ by one (every count is a scan of all 3 Gbp of reads, on both strands):
     window must (count >= d) or must not be in the solid table;
   * the mercy edges of randomly chosen reads, from the paper's rule with the
     solid graph's degrees taken from oracle counts of every neighbour;
+  * the other way round, randomly chosen GPU mercy entries, each traced to
+    the reads holding it (an oracle scan) and justified there by the rule;
 and properties that hold at any size are checked on the whole output (sorted,
-closed under reverse complement on a sample, totals, SdBG block structure).
+closed under reverse complement on a sample, totals, SdBG block structure),
+and the whole SdBG is decoded (tests/sdbg_scan.py) and checked against its
+definitions and the solid + mercy edge set.
 All comparisons are exact (integers).
 """
 import numpy as np
@@ -214,3 +218,89 @@ def test_bucketed_count_matches_in_memory_count(run):
     assert np.array_equal(m["keys"], run["mercy"]["keys"]) and np.array_equal(m["counts"], run["mercy"]["counts"])
     del mercy, solid, reads
     ctx.close()
+
+
+def test_sdbg_full_decode(run):
+    """The whole 3.5e8-entry SdBG decoded and checked against its definitions
+    (tests/sdbg_scan.py, vectorised on the GPU with torch; pinned against
+    oracle/check.py on small graphs): colex order of every node, minus
+    flags, the auxiliary store at zero-indegree vertices, '$' entries at
+    zero-outdegree vertices, F, and decoded edges == solid + mercy exactly."""
+    import torch
+
+    import sdbg_scan
+
+    g, s, m = run["sdbg"], run["solid"], run["mercy"]
+    edges = np.concatenate([s["keys"][:, 0], m["keys"][:, 0]])
+    got = sdbg_scan.check_sdbg_large(g["W"], g["last"], g["dummy"], g["F"], g["aux"], K, edges, device="cuda")
+    assert got["m"] == g["m"] and got["t"] == g["t"] and got["u"] == g["u"] and got["n_nodes"] == g["n_nodes"]
+    assert got["edges"] == len(edges)
+    torch.cuda.empty_cache()
+
+
+def test_sampled_gpu_mercy_edges_are_justified(run):
+    """Every one of 300 randomly sampled GPU mercy entries is justified by a
+    read, from oracle scans of all 3 Gbp (paper, Sec. 2, third paragraph):
+    the entry or its reverse complement occurs as a window of some read,
+    strictly between two consecutive solid windows of that read, the first
+    without a solid successor and the second without a solid predecessor
+    (degrees from oracle counts); and the occurrences add up to the entry's
+    count.  Together with the subset check above, the mercy table is checked
+    in both directions on samples."""
+    s, m = run["solid"], run["mercy"]
+    ascii, offs = run["ascii"], run["offs"]
+    mk = m["keys"][:, 0]
+    rng = np.random.default_rng(4)
+    # sample among entries no larger than their reverse complement, so that no
+    # two sampled queries are the same key
+    idx = []
+    while len(idx) < 300:
+        i = int(rng.integers(0, len(mk)))
+        if int(mk[i]) <= _rc(int(mk[i])) and i not in idx:
+            idx.append(i)
+    idx = np.array(idx)
+    e = mk[idx]
+    rce = np.array([_rc(int(x)) for x in e], dtype=np.uint64)
+    pal = e == rce
+    queries = np.concatenate([e, rce[~pal]])
+    qpos = {int(x): i for i, x in enumerate(queries)}
+    hq, hr, hp = oracle.find_windows(ascii, offs, K, queries.reshape(-1, 1), cap=1 << 16)
+    occ = np.bincount(hq.astype(np.int64), minlength=len(queries))
+    for i in range(len(e)):
+        n_occ = occ[qpos[int(e[i])]] + (0 if pal[i] else occ[qpos[int(rce[i])]])
+        want = 2 * n_occ if pal[i] else n_occ
+        assert want == m["counts"][idx[i]], "mercy entry %d: count vs occurrences" % i
+    # solidity and degrees of every window of the reads holding an occurrence
+    reads = sorted(set(int(r) for r in hr))
+    q = []
+    windows = {}
+    for r in reads:
+        seq = LUT[ascii[int(offs[r]):int(offs[r + 1])]]
+        ws = [_key(seq[i:i + K + 1]) for i in range(len(seq) - K)]
+        windows[r] = ws
+        for x in ws:
+            q.append(x)
+            q.extend(((x << 2) & MASK) | c for c in range(4))
+            q.extend((c << (2 * K)) | (x >> 2) for c in range(4))
+    qa = np.array(q, dtype=np.uint64)
+    uq, inv = np.unique(qa, return_inverse=True)
+    cnt = oracle.count_queries(ascii, offs, K, uq.reshape(-1, 1))[inv]
+    info, pos = {}, 0
+    for r in reads:
+        rows = []
+        for _ in windows[r]:
+            c9 = cnt[pos:pos + 9]
+            pos += 9
+            rows.append((c9[0] >= D, not np.any(c9[1:5] >= D), not np.any(c9[5:9] >= D)))
+        info[r] = rows
+    justified = np.zeros(len(queries), dtype=bool)
+    for qi, r, p in zip(hq.tolist(), hr.tolist(), hp.tolist()):
+        rows = info[r]
+        assert not rows[p][0], "a mercy entry occurs as a solid window"
+        before = [a for a in range(p) if rows[a][0]]
+        after = [b for b in range(p + 1, len(rows)) if rows[b][0]]
+        if before and after and rows[before[-1]][1] and rows[after[0]][2]:
+            justified[qi] = True
+    for i in range(len(e)):
+        ok = justified[qpos[int(e[i])]] or (not pal[i] and justified[qpos[int(rce[i])]])
+        assert ok, "GPU mercy entry %d (key %d) is justified by no read" % (idx[i], int(e[i]))

@@ -270,3 +270,87 @@ def test_count_queries_matches_count():
         absent = oracle.strs_to_keys(["A" * (k + 1)], oracle.words_for(k))
         assert oracle.count_queries(ascii, offs, k, absent)[0] == brute.count(
             [bytes(ascii[offs[i]:offs[i + 1]]) for i in range(len(offs) - 1)], k).get("A" * (k + 1), 0)
+
+
+# --------------------------------------------------- fragments and windows
+
+@pytest.mark.parametrize("seed", [11, 12, 13])
+def test_fragments_match_brute(seed):
+    """orc_fragments (the oracle behind the packing parity) against the
+    brute-force split of each read into maximal ACGT runs, upper-cased:
+    bases, fragment offsets and the read of every fragment, on random reads
+    with N, lower case, empty reads and reads made only of N."""
+    ascii, offs = synth.random_reads(seed, 300, 0, 60, p_invalid=0.08, p_lower=0.3)
+    lens = np.diff(offs)
+    assert (lens == 0).any(), "the case has empty reads"
+    a = bytearray(ascii.tobytes())
+    a[int(offs[5]):int(offs[6])] = b"N" * int(lens[5])   # a read of N only
+    ascii = np.frombuffer(bytes(a), dtype=np.uint8)
+    bases, fo, fr = oracle.fragments(ascii, offs)
+    want_frags, want_read = [], []
+    for r in range(len(offs) - 1):
+        for f in brute.fragments([bytes(ascii[int(offs[r]):int(offs[r + 1])])]):
+            want_frags.append(f)
+            want_read.append(r)
+    want_offs = np.concatenate([[0], np.cumsum([len(f) for f in want_frags])]).astype(np.uint64)
+    assert bases == "".join(want_frags).encode()
+    assert np.array_equal(fo, want_offs)
+    assert np.array_equal(fr, np.array(want_read, dtype=np.uint32))
+
+
+@pytest.mark.parametrize("k", [4, 40])
+def test_find_windows_matches_brute_scan(k):
+    """orc_find_windows against a scan of every read position: a hit is a
+    position whose k+1 bases are all valid (any case) and spell a query."""
+    ascii, offs = synth.random_reads(21 + k, 200, 0, 90, p_invalid=0.03, p_lower=0.2, alphabet=b"ACGT")
+    nw = oracle.words_for(k)
+    rng = np.random.default_rng(k)
+    occ = []
+    for r in range(len(offs) - 1):
+        s = bytes(ascii[int(offs[r]):int(offs[r + 1])]).decode().upper()
+        for p in range(len(s) - k):
+            w = s[p:p + k + 1]
+            if set(w) <= set("ACGT"):
+                occ.append((w, r, p))
+    picked = sorted({occ[i][0] for i in rng.choice(len(occ), size=40, replace=False)})
+    absent = ["".join("ACGT"[c] for c in rng.integers(0, 4, size=k + 1)) for _ in range(10)]
+    strs = picked + [a for a in absent if a not in {o[0] for o in occ}]
+    qi = {s: i for i, s in enumerate(strs)}
+    want = sorted((qi[w], r, p) for w, r, p in occ if w in qi)
+    hq, hr, hp = oracle.find_windows(ascii, offs, k, oracle.strs_to_keys(strs, nw))
+    got = sorted(zip(hq.tolist(), hr.tolist(), hp.tolist()))
+    assert got == want and len(want) >= 40
+
+
+@pytest.mark.parametrize("seed,k,d", [(3, 11, 2), (4, 21, 2), (5, 31, 1)])
+def test_large_decoder_agrees_with_check_sdbg(seed, k, d):
+    """The vectorised decoder that checks the full-size graph
+    (tests/sdbg_scan.py) accepts what check.check_sdbg accepts and rejects
+    every planted mistake that check.check_sdbg rejects (k = 31 with d = 1,
+    so that error k-mers make targets with several in-edges)."""
+    import sdbg_scan
+
+    ascii, offs = synth.uniform_genome_reads(seed, 2000, 300, 60, 0.01)
+    r = oracle.count(ascii, offs, k, d, mercy=True)
+    edges = np.concatenate([r["solid_keys"], r["mercy_keys"]])
+    sd = oracle.build_sdbg(k, r["solid_keys"], r["solid_cnt"], r["mercy_keys"], r["mercy_cnt"])
+    assert np.any(sd["W"] > 4) and sd["t"] >= 2
+    check.check_sdbg(sd, k, edges)
+    got = sdbg_scan.check_sdbg_large(sd["W"], sd["last"], sd["dummy"], sd["F"], sd["aux"], k, edges)
+    assert got["m"] == sd["m"] and got["t"] == sd["t"] and got["u"] == sd["u"] and got["n_nodes"] == sd["n_nodes"]
+    shuffled = edges[np.random.default_rng(seed).permutation(len(edges))]
+    sdbg_scan.check_sdbg_large(sd["W"], sd["last"], sd["dummy"], sd["F"], sd["aux"], k, shuffled)
+    planted = 0
+    for name, bad in _corruptions(sd):
+        try:
+            check.check_sdbg(bad, k, edges)
+            continue  # the slip changed nothing here (e.g. two equal entries swapped)
+        except AssertionError:
+            planted += 1
+        with pytest.raises(AssertionError):
+            sdbg_scan.check_sdbg_large(bad["W"], bad["last"], bad["dummy"], bad["F"], bad["aux"], k, edges)
+            raise RuntimeError("planted mistake not caught: " + name)
+    assert planted >= 4
+    # an edge missing from the graph
+    with pytest.raises(AssertionError):
+        sdbg_scan.check_sdbg_large(sd["W"], sd["last"], sd["dummy"], sd["F"], sd["aux"], k, edges[1:])
