@@ -76,8 +76,10 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="metagenome",
                    choices=sorted(WORKLOADS) + ["multik", "served", "batched"])
-    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=4)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the bounded served and batched runs the default metagenome line carries")
     p.add_argument("--workers", type=int, default=None, help="worker streams of the batched workload (4)")
     p.add_argument("--torch-alloc", action="store_true",
                    help="library buffers from torch's caching allocator in every workload")
@@ -347,23 +349,18 @@ BATCHED = {
 }
 
 
-def run_batched(args, rank, world, local):
-    """One step = the whole path on all 64 read sets through mh_run_batch
-    (worker streams, largest set first); value = (k+1)-mers of all sets per
-    second.  The same sets through the plain calls one after another on one
-    stream are timed beside it (serial_value)."""
+def batched_figures(local, n_sets, steps, warmup, workers, seed=None):
+    """The batched workload on `n_sets` sets: the whole path on every set
+    through mh_run_batch (worker streams, largest set first, tile shape
+    autotuned), against the same sets through the plain calls one after
+    another on one stream.  Returns a dict of the figures."""
     import numpy as np
     import torch
 
     import paper_1409_7208_gb300 as mh
     import synth
 
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    sets = synth.batch_sets(BATCHED["seed"] + 1000 * rank, BATCHED["n_sets"])
+    sets = synth.batch_sets(BATCHED["seed"] if seed is None else seed, n_sets)
     n_reads = sum(len(o) - 1 for _, o in sets)
     n_bases = sum(len(a) for a, _ in sets)
     stream = torch.cuda.Stream(device=local)
@@ -371,16 +368,13 @@ def run_batched(args, rank, world, local):
     ctx = mh.Context(device=local, stream=stream, torch_allocator=False)
     dev = [(torch.from_numpy(a).cuda(), torch.from_numpy(o.view(np.int64)).cuda()) for a, o in sets]
     torch.cuda.synchronize()
-    k, d, W = BATCHED["k"], BATCHED["d"], args.workers or BATCHED["workers"]
+    k, d = BATCHED["k"], BATCHED["d"]
     info = {}
 
-    def batched(inputs, download=None):
-        res = mh.mh_run_batch(ctx, inputs, k, d, workers=W, autotune=True)
+    def batched(inputs):
+        res = mh.mh_run_batch(ctx, inputs, k, d, workers=workers, autotune=True)
         info["n_kmers"] = sum(r["solid"].view().n_kmers for r in res)
         info["m"] = sum(r["sdbg"].view().m for r in res)
-        if download is not None:
-            for r in res:
-                download(r["sdbg"])
         for r in res:
             for key in ("sdbg", "mercy", "solid"):
                 r[key].free()
@@ -403,26 +397,53 @@ def run_batched(args, rank, world, local):
         torch.cuda.synchronize()
         return ev0.elapsed_time(ev1) / n
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batched(dev)
-    if dist is not None:
-        dist.barrier()
-    # the plain path, one set after another (kernels alone: the roofline)
     serial(dev)
     ctx.profile_reset()
     ctx.set_profile(True)
     serial_ms = timed(lambda: serial(dev), 1)
     ctx.set_profile(False)
     prof_serial = ctx.profile()
-    clocks = Clocks(local)
-    clocks.start()
     ctx.profile_reset()
     ctx.set_profile(True)
-    ms = timed(lambda: batched(dev), args.steps)
+    ms = timed(lambda: batched(dev), steps)
     ctx.set_profile(False)
-    clk = clocks.stop()
     prof = ctx.profile()
-    tot = job_totals(dist, "cuda", info["n_kmers"], info["m"], ms)
+    out = {"sets": len(sets), "reads": n_reads, "bases": n_bases, "k": k, "d": d, "workers": workers,
+           "sort_shape": mh.mh_sort_shape(ctx), "ms": ms, "serial_ms": serial_ms,
+           "kmers_per_s": info["n_kmers"] / (ms / 1e3), "serial_kmers_per_s": info["n_kmers"] / (serial_ms / 1e3),
+           "jobs_per_s": len(sets) / (ms / 1e3), "serial_jobs_per_s": len(sets) / (serial_ms / 1e3),
+           "batch_speedup": serial_ms / ms, "n_kmers": info["n_kmers"], "m": info["m"],
+           "prof": prof, "prof_serial": prof_serial, "sets_data": sets, "ctx": ctx, "stream": stream,
+           "dev": dev, "batched_fn": batched}
+    return out
+
+
+def run_batched(args, rank, world, local):
+    """One step = the whole path on all 64 read sets through mh_run_batch
+    (worker streams, largest set first); value = (k+1)-mers of all sets per
+    second.  The same sets through the plain calls one after another on one
+    stream are timed beside it (serial_value)."""
+    import numpy as np
+    import torch
+
+    import paper_1409_7208_gb300 as mh
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    W = args.workers or BATCHED["workers"]
+    clocks = Clocks(local)
+    clocks.start()
+    f = batched_figures(local, BATCHED["n_sets"], args.steps, args.warmup, W, BATCHED["seed"] + 1000 * rank)
+    clk = clocks.stop()
+    sets, ctx, stream, batched = f["sets_data"], f["ctx"], f["stream"], f["batched_fn"]
+    n_reads, n_bases, k, d = f["reads"], f["bases"], f["k"], f["d"]
+    prof, prof_serial = f["prof"], f["prof_serial"]
+    tot = job_totals(dist, "cuda", f["n_kmers"], f["m"], f["ms"])
     ms = tot["ms"]
     value = tot["kmers"] / (ms / 1e3)
 
@@ -443,15 +464,23 @@ def run_batched(args, rank, world, local):
                     nbytes["d2h"] += src.numel() * src.element_size()
             stream.synchronize()
 
-        batched(pinned, download)
+        def batched_dl(inputs):
+            res = mh.mh_run_batch(ctx, inputs, k, d, workers=W, autotune=True)
+            for r in res:
+                download(r["sdbg"])
+            for r in res:
+                for key in ("sdbg", "mercy", "solid"):
+                    r[key].free()
+
+        batched_dl(pinned)
         torch.cuda.synchronize()
         nbytes["d2h"] = 0
         e0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            batched(pinned, download)
+            batched_dl(pinned)
         torch.cuda.synchronize()
         e_s = (time.perf_counter() - e0) / args.e2e_steps
-        e2e = {"value": info["n_kmers"] / e_s, "unit": UNIT,
+        e2e = {"value": f["n_kmers"] / e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(n_bases + 8 * (n_reads + len(sets))),
                "d2h_bytes_per_step": int(nbytes["d2h"] / args.e2e_steps + 48 * len(sets))}
 
@@ -478,10 +507,10 @@ def run_batched(args, rank, world, local):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                 "config": {"workload": BATCHED["name"], "sets": len(sets), "reads": n_reads, "bases": n_bases,
-                           "k": k, "d": d, "workers": W, "sort_shape": mh.mh_sort_shape(ctx),
+                           "k": k, "d": d, "workers": W, "sort_shape": f["sort_shape"],
                            "l2": "inputs larger than L2 (%.1f GB of reads)" % (n_bases / 1e9)},
-                "serial_value": info["n_kmers"] / (serial_ms / 1e3), "serial_ms": serial_ms,
-                "batch_speedup": serial_ms / ms,
+                "serial_value": f["serial_kmers_per_s"], "serial_ms": f["serial_ms"],
+                "batch_speedup": f["batch_speedup"],
                 "sdbg_edges_per_s": tot["edges"] / (ms / 1e3),
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": sum(la for (la, _, _) in prof.values()) // args.steps * args.steps,
@@ -502,7 +531,7 @@ SERVED = {
 }
 
 
-def _served_pool(seed):
+def _served_pool(seed, size):
     """The distinct read sets the jobs draw from: sizes from the served
     distribution, each its own uniform genome at 20x, in pinned host memory."""
     import numpy as np
@@ -511,7 +540,7 @@ def _served_pool(seed):
     import synth
     rng = np.random.default_rng(seed)
     pool = []
-    for i in range(SERVED["pool"]):
+    for i in range(size):
         n = int(np.clip(rng.lognormal(np.log(SERVED["median"]), SERVED["sigma"]), SERVED["lo"], SERVED["hi"]))
         L = int(rng.integers(100, 151))
         ascii, offs = synth.uniform_genome_reads(int(rng.integers(1 << 30)), max(5000, n * L // 20), n, L, 0.005)
@@ -557,29 +586,29 @@ def _run_stream(jobs, slots, budget, runner, paced):
     return t1 - t0, srv.max_held
 
 
-def run_served(args, rank, local):
+def served_figures(local, secs, pool_size, warmup, cpu_baseline):
+    """The served workload: a Poisson stream over `secs` seconds of jobs drawn
+    from a pool of `pool_size` read sets, submitted at their arrival times to
+    the serving loop (4 slots, HBM budget); then the same jobs all queued at
+    once on the 4 slots, and one at a time through the plain path (one slot).
+    Returns a dict of the figures."""
     import numpy as np
-    import torch
 
     from paper_1409_7208_gb300 import serve
-    if rank != 0:
-        return
-    torch.cuda.set_device(local)
+    t_gen = time.perf_counter()
     runner = serve.DeviceRunner(local, SERVED["slots"])
-    pool = _served_pool(SERVED["seed"])
+    pool = _served_pool(SERVED["seed"], pool_size)
+    t_gen = time.perf_counter() - t_gen
     warm = _served_jobs(pool, SERVED["seed"] + 100, 0.5)
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         for j in warm:
             j.__init__(j.ascii, j.offs, j.k, j.d, j.tag)
         _run_stream(warm, SERVED["slots"], SERVED["budget"], runner, False)
-    jobs = _served_jobs(pool, SERVED["seed"], SERVED["secs"])
+    jobs = _served_jobs(pool, SERVED["seed"], secs)
     for c in runner.ctxs:
         c.profile_reset()
         c.set_profile(True)
-    clocks = Clocks(local)
-    clocks.start()
     wall, held = _run_stream(jobs, SERVED["slots"], SERVED["budget"], runner, True)
-    clk = clocks.stop()
     for c in runner.ctxs:
         c.set_profile(False)
     lat = np.array([j.latency for j in jobs]) * 1e3
@@ -601,7 +630,7 @@ def run_served(args, rank, local):
     serial_wall, _ = _run_stream(jobs, 1, SERVED["budget"], runner, False)
     svc = np.array([j.end_t - j.start_t for j in jobs]) * 1e3
     cpu = None
-    if not args.no_cpu_baseline:
+    if cpu_baseline:
         small = sorted(jobs, key=lambda j: j.n_bases)[:3]
         t_c = 0.0
         for j in small:
@@ -609,32 +638,48 @@ def run_served(args, rank, local):
         cpu = {"value": len(small) / t_c, "unit": "jobs/s", "cores": 1, "kind": "oracle",
                "sample": "the 3 smallest jobs of the stream (%d reads), %.1f s"
                          % (sum(j.n_reads for j in small), t_c)}
-    peak, peak_kind = _peak_hbm()
-    la, o_ms, o_bytes = prof.get("radix_onesweep", (0, 0.0, 0))
-    achieved = o_bytes / (o_ms / 1e3) / 1e9 if o_ms > 0 else 0.0
-    line = {"metric": METRIC, "value": len(jobs) / wall, "unit": "jobs/s", "n_gpus": 1, "steps": 1,
-            "warmup": args.warmup, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": SERVED["name"], "jobs": len(jobs), "reads": int(sum(j.n_reads for j in jobs)),
-                       "bases": int(sum(j.n_bases for j in jobs))},
+    runner.close()
+    return {"secs": secs, "pool": pool_size, "jobs": len(jobs), "reads": int(sum(j.n_reads for j in jobs)),
+            "bases": int(sum(j.n_bases for j in jobs)), "wall_s": wall, "jobs_per_s": len(jobs) / wall,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "kmers_per_s": kmers / wall, "max_held_bytes": int(held),
             "serial": {"jobs_per_s": len(jobs) / serial_wall, "service_p50_ms": float(np.percentile(svc, 50)),
                        "service_p99_ms": float(np.percentile(svc, 99))},
             "burst": {"jobs_per_s": len(jobs) / burst_wall, "slots": SERVED["slots"],
-                      "vs_serial": serial_wall / burst_wall,
-                      "note": "every job of the stream queued at once"},
+                      "vs_serial": serial_wall / burst_wall, "note": "every job of the stream queued at once"},
+            "pool_generation_s": t_gen, "prof": prof, "cpu": cpu,
+            "h2d_bytes": int(sum(j.n_bases + 8 * (j.n_reads + 1) for j in jobs))}
+
+
+def run_served(args, rank, local):
+    import torch
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    clocks = Clocks(local)
+    clocks.start()
+    f = served_figures(local, SERVED["secs"], SERVED["pool"], args.warmup, not args.no_cpu_baseline)
+    clk = clocks.stop()
+    prof = f["prof"]
+    peak, peak_kind = _peak_hbm()
+    la, o_ms, o_bytes = prof.get("radix_onesweep", (0, 0.0, 0))
+    achieved = o_bytes / (o_ms / 1e3) / 1e9 if o_ms > 0 else 0.0
+    line = {"metric": METRIC, "value": f["jobs_per_s"], "unit": "jobs/s", "n_gpus": 1, "steps": 1,
+            "warmup": args.warmup, "ms_per_step": f["wall_s"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": SERVED["name"], "jobs": f["jobs"], "reads": f["reads"], "bases": f["bases"]},
+            "p50_ms": f["p50_ms"], "p99_ms": f["p99_ms"], "kmers_per_s": f["kmers_per_s"],
+            "max_held_bytes": f["max_held_bytes"], "serial": f["serial"], "burst": f["burst"],
             "roofline": {"bound": "hbm", "kernel": "radix_onesweep", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                          "note": "concurrent launches on 4 streams: per-launch times overlap"},
-            "cpu_baseline": cpu,
-            "e2e": {"value": len(jobs) / wall, "unit": "jobs/s",
-                    "h2d_bytes_per_step": int(sum(j.n_bases + 8 * (j.n_reads + 1) for j in jobs)),
+            "cpu_baseline": f["cpu"],
+            "e2e": {"value": f["jobs_per_s"], "unit": "jobs/s", "h2d_bytes_per_step": f["h2d_bytes"],
                     "d2h_bytes_per_step": 0,
                     "note": "reads come from host memory in every job; results stay resident until released"},
             "gpu_launches": int(sum(p[0] for p in prof.values())), "clocks": clk}
     print(json.dumps(line), flush=True)
-    runner.close()
 
 
 def main():
@@ -809,7 +854,7 @@ def main():
     d2h = {"bytes": 0}
     host_bufs = {}
 
-    def download(g):
+    def download(g, ev=None):
         t = g.tensors()
         nbytes = 0
         with torch.cuda.stream(stream):  # copies in order behind the library's work
@@ -822,6 +867,8 @@ def main():
                 if src.numel():
                     buf[: src.numel()].view(src.shape).copy_(src, non_blocking=True)
                 nbytes += src.numel() * src.element_size()
+        if ev is not None:
+            ev.record(stream)
         stream.synchronize()
         d2h["bytes"] = nbytes + 48  # + F, returned by value
 
@@ -830,16 +877,75 @@ def main():
         step(pin_ascii, pin_offs, None, download)  # warm the host path
         torch.cuda.synchronize()
         barrier()
+        h2d = int(n_bases + offs.nbytes)
+        # one step with the library's own host-input path (mh_pack_reads from
+        # pinned host memory: staged copy overlapped with the packing), timed
+        # part by part
+        h0 = time.perf_counter()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        reads = mh.mh_pack_reads(ctx, pin_ascii, pin_offs)
+        ev[1].record(stream)
+        solid = mh.mh_count_kmers(ctx, reads, k, d)
+        mercy = mh.mh_mercy_kmers(ctx, reads, solid)
+        g = mh.mh_build_sdbg(ctx, solid, mercy)
+        ev[2].record(stream)
+        download(g, ev[3])
+        del g, mercy, solid, reads
+        wall = 1e3 * (time.perf_counter() - h0)
+        up, comp, down = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])
+        serial = {"step_ms": wall, "upload_ms": up, "upload_GBps": h2d / (up / 1e3) / 1e9 if up else None,
+                  "compute_ms": comp, "download_ms": down,
+                  "download_GBps": d2h["bytes"] / (down / 1e3) / 1e9 if down else None,
+                  "host_wait_ms": wall - ev[0].elapsed_time(ev[3])}
+        # the timed end-to-end steps: each step's reads go up from pinned host
+        # memory into one of two device buffers on a copy stream while the
+        # step before computes (the first upload is not overlapped); then the
+        # same calls on device pointers, and the SdBG arrays come back
+        up_stream = torch.cuda.Stream(device=local)
+        dbuf = [(torch.empty(n_bases, dtype=torch.uint8, device="cuda"),
+                 torch.empty(offs.shape[0], dtype=torch.int64, device="cuda")) for _ in range(2)]
+        up_done = [torch.cuda.Event() for _ in range(2)]
+        buf_free = [torch.cuda.Event() for _ in range(2)]
+        for e in buf_free:
+            e.record(stream)
+
+        def upload(i):
+            with torch.cuda.stream(up_stream):
+                up_stream.wait_event(buf_free[i % 2])
+                dbuf[i % 2][0].copy_(pin_ascii, non_blocking=True)
+                dbuf[i % 2][1].copy_(pin_offs, non_blocking=True)
+                up_done[i % 2].record(up_stream)
+
+        torch.cuda.synchronize()
+        barrier()
         e0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            step(pin_ascii, pin_offs, None, download)
+        upload(0)
+        for i in range(args.e2e_steps):
+            if i + 1 < args.e2e_steps:
+                upload(i + 1)
+            stream.wait_event(up_done[i % 2])
+            reads = mh.mh_pack_reads(ctx, dbuf[i % 2][0], dbuf[i % 2][1])
+            buf_free[i % 2].record(stream)
+            solid = mh.mh_count_kmers(ctx, reads, k, d)
+            mercy = mh.mh_mercy_kmers(ctx, reads, solid)
+            g = mh.mh_build_sdbg(ctx, solid, mercy)
+            download(g)
+            del g, mercy, solid, reads
         torch.cuda.synchronize()
         e_s = time.perf_counter() - e0
         e_tot = job_totals(dist, "cuda", info["n_kmers"], info["m"], 0.0, e_s)
         e_s = e_tot["e2e_s"]
         e2e = {"value": e_tot["kmers"] * args.e2e_steps / e_s, "unit": UNIT,
-               "h2d_bytes_per_step": int(n_bases + offs.nbytes), "d2h_bytes_per_step": int(d2h["bytes"])}
-
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(d2h["bytes"]),
+               "step_ms": 1e3 * e_s / args.e2e_steps,
+               "upload_ms": serial["upload_ms"], "upload_GBps": serial["upload_GBps"],
+               "download_ms": serial["download_ms"], "host_wait_ms": serial["host_wait_ms"],
+               "how": "per step: the reads' upload from pinned host memory (overlapped with the previous "
+                      "step's compute, the first one not), pack + count + mercy + build through the C ABI, "
+                      "the SdBG arrays back to pinned host memory; upload/download/host-wait figures from "
+                      "one further step through the library's host-input path, timed part by part",
+               "serial_step": serial}
     # roofline of the dominant kernel (radix scatter pass)
     peak, peak_kind = _peak_hbm()
     launches, o_ms, o_bytes = prof.get("radix_onesweep", (0, 0.0, 0))
@@ -891,10 +997,53 @@ def main():
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clk,
         }
-        print(json.dumps(line), flush=True)
     ctx.close()
+    if rank == 0 and world == 1 and args.workload == "metagenome" and not args.no_extras:
+        # the NEXT rows' forms on the same GPU, bounded (a few minutes in all):
+        # the served stream (jobs/s, p50/p99) against the same jobs through
+        # the plain path one at a time, and the batched sets against the plain
+        # path one set after another
+        del d_ascii, d_offs
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        line["served"] = _served_extra(local, args)
+        torch.cuda.empty_cache()
+        line["batched"] = _batched_extra(local, args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+EXTRA_SERVED_SECS = 20.0
+EXTRA_SERVED_POOL = 32
+EXTRA_BATCHED_STEPS = 2
+
+
+def _served_extra(local, args):
+    f = served_figures(local, EXTRA_SERVED_SECS, EXTRA_SERVED_POOL, 1, False)
+    return {"workload": "the served stream (arrivals 20/s) over %.0f s instead of 60, jobs drawn from a pool of "
+                        "%d read sets instead of 96; otherwise as the served config" % (EXTRA_SERVED_SECS,
+                                                                                   EXTRA_SERVED_POOL),
+            "jobs": f["jobs"], "jobs_per_s": f["jobs_per_s"], "p50_ms": f["p50_ms"], "p99_ms": f["p99_ms"],
+            "kmers_per_s": f["kmers_per_s"], "serial_jobs_per_s": f["serial"]["jobs_per_s"],
+            "burst_jobs_per_s": f["burst"]["jobs_per_s"], "burst_vs_serial": f["burst"]["vs_serial"],
+            "max_held_GB": round(f["max_held_bytes"] / 1e9, 1)}
+
+
+def _batched_extra(local, args):
+    import torch
+
+    f = batched_figures(local, BATCHED["n_sets"], EXTRA_BATCHED_STEPS, 1, BATCHED["workers"])
+    out = {"workload": "the batched config (64 sets), %d timed batches" % EXTRA_BATCHED_STEPS,
+           "sets": f["sets"], "reads": f["reads"], "ms": f["ms"], "serial_ms": f["serial_ms"],
+           "jobs_per_s": f["jobs_per_s"], "serial_jobs_per_s": f["serial_jobs_per_s"],
+           "kmers_per_s": f["kmers_per_s"], "serial_kmers_per_s": f["serial_kmers_per_s"],
+           "batch_speedup": f["batch_speedup"], "sort_shape": f["sort_shape"]}
+    f["ctx"].close()
+    del f
+    torch.cuda.empty_cache()
+    return out
 
 
 if __name__ == "__main__":

@@ -247,4 +247,3 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
 }
 
 }  // namespace mh
-
