@@ -188,12 +188,47 @@ def job_totals(dist, device, kmers: int, edges: int, ms: float, e2e_s: float = 0
             "e2e_s": float(maxs[1].item())}
 
 
-def cpu_oracle_run(ascii, offs, k, d):
+def cpu_oracle_run(ascii, offs, k, d, threads=1):
     import oracle
     t0 = time.perf_counter()
-    r = oracle.count(ascii, offs, k, d, mercy=True)
+    r = oracle.count(ascii, offs, k, d, mercy=True, threads=threads)
     oracle.build_sdbg(k, r["solid_keys"], r["solid_cnt"], r["mercy_keys"], r["mercy_cnt"])
     return r["n_kmers"], time.perf_counter() - t0
+
+
+def _host_cpu():
+    """(cores, model) of the host the oracle runs on."""
+    n = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return n, model or "unknown"
+
+
+def cpu_baseline_pair(ascii, offs, k, d, sample):
+    """The oracle on the sample on every host core (counting split by prefix,
+    mercy by fragment; the SdBG build one thread) and on one core."""
+    n_cores, model = _host_cpu()
+    n1, t1 = cpu_oracle_run(ascii, offs, k, d, 1)
+    nn, tn = cpu_oracle_run(ascii, offs, k, d, n_cores)
+    return {"value": nn / tn, "unit": UNIT, "cores": n_cores, "kind": "oracle", "sample": sample,
+            "seconds": tn, "one_thread": {"value": n1 / t1, "cores": 1, "seconds": t1},
+            "nproc": n_cores, "cpu_model": model,
+            "note": "value: counting and mercy on every core, the SdBG build on one"}
 
 
 def run_reference(args, wl, rank, world):
@@ -201,21 +236,23 @@ def run_reference(args, wl, rank, world):
     if rank != 0:
         return
     ascii, offs = wl["sample"](wl["seed"], CPU_SAMPLE_READS)
+    n_cores, model = _host_cpu()
     for _ in range(args.warmup):
-        cpu_oracle_run(ascii, offs, wl["k"], wl["d"])
+        cpu_oracle_run(ascii, offs, wl["k"], wl["d"], n_cores)
     total_n, total_t = 0, 0.0
     for _ in range(args.steps):
-        n, t = cpu_oracle_run(ascii, offs, wl["k"], wl["d"])
+        n, t = cpu_oracle_run(ascii, offs, wl["k"], wl["d"], n_cores)
         total_n += n
         total_t += t
     v = total_n / total_t
-    sample = "first %d reads of the workload (%d (k+1)-mers on both strands)" % (len(offs) - 1, n)
+    sample = ("first %d reads of the workload (%d (k+1)-mers on both strands); counting and mercy on %d "
+              "threads (%s), the SdBG build on one" % (len(offs) - 1, n, n_cores, model))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic", "config": {"workload": wl["name"], "k": wl["k"], "d": wl["d"],
                                             "sample_reads": len(offs) - 1},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": n_cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -499,9 +536,7 @@ def run_batched(args, rank, world, local):
         sa, so = sets[0]
         ns = min(CPU_SAMPLE_READS, len(so) - 1)
         sa, so = sa[: int(so[ns])], so[: ns + 1]
-        n_s, t_s = cpu_oracle_run(sa, so, k, d)
-        cpu = {"value": n_s / t_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "first %d reads of set 0 (%d (k+1)-mers on both strands), %.1f s" % (ns, n_s, t_s)}
+        cpu = cpu_baseline_pair(sa, so, k, d, "first %d reads of set 0" % ns)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -699,11 +734,12 @@ def main():
                 sa, so = synth.batch_sets(BATCHED["seed"], 1)[0]
                 ns = min(CPU_SAMPLE_READS, len(so) - 1)
                 sa, so = sa[: int(so[ns])], so[: ns + 1]
+                n_cores, model = _host_cpu()
                 for _ in range(args.warmup):
-                    cpu_oracle_run(sa, so, BATCHED["k"], BATCHED["d"])
+                    cpu_oracle_run(sa, so, BATCHED["k"], BATCHED["d"], n_cores)
                 n_s = t_s = 0
                 for _ in range(args.steps):
-                    n, t = cpu_oracle_run(sa, so, BATCHED["k"], BATCHED["d"])
+                    n, t = cpu_oracle_run(sa, so, BATCHED["k"], BATCHED["d"], n_cores)
                     n_s += n
                     t_s += t
                 v = n_s / t_s
@@ -712,8 +748,10 @@ def main():
                                   "ms_per_step": 1e3 * t_s / args.steps, "higher_is_better": True,
                                   "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                                   "config": {"workload": BATCHED["name"], "sample_reads": ns},
-                                  "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                                   "sample": "first %d reads of set 0" % ns},
+                                  "cpu_baseline": {"value": v, "unit": UNIT, "cores": n_cores, "kind": "oracle",
+                                                   "sample": "first %d reads of set 0; counting and mercy on "
+                                                             "%d threads (%s), the SdBG build on one"
+                                                             % (ns, n_cores, model)},
                                   "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                                           "d2h_bytes_per_step": 0}}), flush=True)
             return
@@ -971,10 +1009,8 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         sa, so = wl["sample"](wl["seed"], CPU_SAMPLE_READS)
-        n_s, t_s = cpu_oracle_run(sa, so, k, d)
-        cpu = {"value": n_s / t_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "first %d reads of the workload (%d (k+1)-mers on both strands), %.1f s"
-                         % (len(so) - 1, n_s, t_s)}
+        cpu = cpu_baseline_pair(sa, so, k, d, "first %d reads of the workload (%d (k+1)-mers on both strands)"
+                                % (len(so) - 1, 2 * int(np.maximum(np.diff(so).astype(np.int64) - k, 0).sum())))
 
     if rank == 0:
         line = {

@@ -69,6 +69,9 @@ def _load():
                                ctypes.POINTER(ctypes.c_uint32))
             lib.orc_count.argtypes = [u8p, u64p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             lib.orc_count.restype = ctypes.POINTER(_KmerResult)
+            lib.orc_count_threaded.argtypes = [u8p, u64p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_int]
+            lib.orc_count_threaded.restype = ctypes.POINTER(_KmerResult)
             lib.orc_free_kmer_result.argtypes = [ctypes.POINTER(_KmerResult)]
             lib.orc_build_sdbg.argtypes = [ctypes.c_int, u64p, u32p, ctypes.c_uint64, u64p, u32p,
                                            ctypes.c_uint64]
@@ -118,8 +121,10 @@ def fragments(ascii, offs):
     return buf.raw[:total], fo[:nf + 1].copy(), fr[:nf].copy()
 
 
-def count(ascii, offs, k: int, d: int = 2, mercy: bool = True) -> dict:
+def count(ascii, offs, k: int, d: int = 2, mercy: bool = True, threads: int = 1) -> dict:
     """Solid (k+1)-mers with counts and, if ``mercy``, mercy (k+1)-mers.
+    ``threads`` > 1: the same computation split by 8-symbol prefix over that
+    many threads (counting) and by fragment (mercy).
 
     Returns ``solid_keys`` (S x nw uint64, ascending), ``solid_cnt`` (uint32),
     ``mercy_keys``/``mercy_cnt`` likewise, ``n_kmers`` = |K| (both strands)
@@ -131,8 +136,12 @@ def count(ascii, offs, k: int, d: int = 2, mercy: bool = True) -> dict:
     n_reads = len(offs) - 1
     if len(ascii) == 0:
         ascii = np.zeros(1, dtype=np.uint8)
-    r = lib.orc_count(_p(ascii, ctypes.c_uint8), _p(offs, ctypes.c_uint64), n_reads, k, d,
-                      1 if mercy else 0)
+    if threads > 1:
+        r = lib.orc_count_threaded(_p(ascii, ctypes.c_uint8), _p(offs, ctypes.c_uint64), n_reads, k, d,
+                                   1 if mercy else 0, int(threads))
+    else:
+        r = lib.orc_count(_p(ascii, ctypes.c_uint8), _p(offs, ctypes.c_uint64), n_reads, k, d,
+                          1 if mercy else 0)
     try:
         c = r.contents
         if c.status != 0:

@@ -281,6 +281,111 @@ orc_kmer_result* orc_count(const uint8_t* ascii, const uint64_t* offs, uint64_t 
     return r;
 }
 
+// The same counting and mercy as orc_count, spread over n_threads threads
+// (the threaded CPU baseline).  Counting: thread t takes the (k+1)-mers whose
+// first 8 symbols (as a number, 4^8 buckets) fall in its range of buckets,
+// from both strands of every fragment, and sorts and counts them alone; the
+// threads' outputs, in thread order, are the whole sorted table.  Mercy: the
+// fragments are split between the threads, each scans its own against the
+// shared solid set; the edges found are merged and closed under reverse
+// complement.  Same outputs as orc_count.
+orc_kmer_result* orc_count_threaded(const uint8_t* ascii, const uint64_t* offs, uint64_t n_reads, int k, int d,
+                                    int do_mercy, int n_threads) {
+    orc_kmer_result* r = (orc_kmer_result*)calloc(1, sizeof(orc_kmer_result));
+    if (k < 2 || k > 127 || d < 1) { r->status = -1; return r; }
+    if (n_threads < 1) n_threads = 1;
+    r->k = k;
+    r->nw = words_for(k);
+    std::vector<std::string> frags = fragments(ascii, offs, n_reads);
+    const int pl = k + 1 < 8 ? k + 1 : 8;  // prefix symbols that pick the bucket
+    const uint64_t n_buckets = 1ull << (2 * pl);
+    // bucket of the string of symbols f[p..p+pl) read forward, or of the
+    // reverse complement of the window ending at p + k (its first pl symbols
+    // are the complements of the window's last pl symbols, last first)
+    auto fwd_bucket = [&](const std::string& f, size_t p) {
+        uint64_t b = 0;
+        for (int i = 0; i < pl; i++) b = b * 4 + (uint64_t)code_of(f[p + i]);
+        return b;
+    };
+    auto rc_bucket = [&](const std::string& f, size_t p) {
+        uint64_t b = 0;
+        for (int i = 0; i < pl; i++) b = b * 4 + (uint64_t)(3 - code_of(f[p + k - i]));
+        return b;
+    };
+    std::vector<Counted> part(n_threads);
+    auto count_part = [&](int t) {
+        const uint64_t lo = n_buckets * t / n_threads, hi = n_buckets * (t + 1) / n_threads;
+        std::vector<std::string> K;
+        for (const std::string& f : frags) {
+            if ((int)f.size() < k + 1) continue;
+            for (size_t i = 0; i + k < f.size(); i++) {
+                const uint64_t bf = fwd_bucket(f, i), br = rc_bucket(f, i);
+                if (bf >= lo && bf < hi) K.push_back(f.substr(i, k + 1));
+                if (br >= lo && br < hi) K.push_back(reverse_complement(f.substr(i, k + 1)));
+            }
+        }
+        std::sort(K.begin(), K.end());
+        Counted& c = part[t];
+        c.n_kmers = K.size();
+        for (size_t i = 0; i < K.size();) {
+            size_t j = i;
+            while (j < K.size() && K[j] == K[i]) j++;
+            c.keys.push_back(K[i]);
+            c.cnt.push_back(j - i);
+            i = j;
+        }
+    };
+    {
+        std::vector<std::thread> th;
+        for (int t = 0; t < n_threads; t++) th.emplace_back(count_part, t);
+        for (auto& x : th) x.join();
+    }
+    Counted c;
+    for (Counted& p : part) {
+        c.n_kmers += p.n_kmers;
+        c.keys.insert(c.keys.end(), p.keys.begin(), p.keys.end());
+        c.cnt.insert(c.cnt.end(), p.cnt.begin(), p.cnt.end());
+    }
+    r->n_kmers = c.n_kmers;
+    r->n_distinct = c.keys.size();
+    std::vector<std::string> solid;
+    std::vector<uint32_t> solid_cnt;
+    for (size_t i = 0; i < c.keys.size(); i++) {
+        if (c.cnt[i] > 0xFFFFFFFFull) { r->status = -3; return r; }
+        if (c.cnt[i] >= (uint64_t)d) {
+            solid.push_back(c.keys[i]);
+            solid_cnt.push_back((uint32_t)c.cnt[i]);
+        }
+    }
+    r->n_solid = solid.size();
+    put_keys(solid, r->nw, &r->solid_keys);
+    r->solid_cnt = (uint32_t*)calloc(solid.size() + 1, sizeof(uint32_t));
+    std::copy(solid_cnt.begin(), solid_cnt.end(), r->solid_cnt);
+    if (do_mercy) {
+        std::set<std::string> solid_set(solid.begin(), solid.end());
+        std::vector<std::vector<std::string>> found(n_threads);
+        auto mercy_part = [&](int t) {
+            const size_t f0 = frags.size() * t / n_threads, f1 = frags.size() * (t + 1) / n_threads;
+            std::vector<std::string> mine(frags.begin() + f0, frags.begin() + f1);
+            found[t] = mercy_edges(mine, k, solid_set);
+        };
+        std::vector<std::thread> th;
+        for (int t = 0; t < n_threads; t++) th.emplace_back(mercy_part, t);
+        for (auto& x : th) x.join();
+        std::set<std::string> all;
+        for (auto& v : found) all.insert(v.begin(), v.end());
+        std::vector<std::string> mercy(all.begin(), all.end());
+        r->n_mercy = mercy.size();
+        put_keys(mercy, r->nw, &r->mercy_keys);
+        r->mercy_cnt = (uint32_t*)calloc(mercy.size() + 1, sizeof(uint32_t));
+        for (size_t i = 0; i < mercy.size(); i++) {
+            const size_t j = std::lower_bound(c.keys.begin(), c.keys.end(), mercy[i]) - c.keys.begin();
+            r->mercy_cnt[i] = (uint32_t)c.cnt[j];
+        }
+    }
+    return r;
+}
+
 void orc_free_kmer_result(orc_kmer_result* r) {
     if (!r) return;
     free(r->solid_keys);

@@ -354,3 +354,18 @@ def test_large_decoder_agrees_with_check_sdbg(seed, k, d):
     # an edge missing from the graph
     with pytest.raises(AssertionError):
         sdbg_scan.check_sdbg_large(sd["W"], sd["last"], sd["dummy"], sd["F"], sd["aux"], k, edges[1:])
+
+
+@pytest.mark.parametrize("k,threads", [(2, 3), (7, 8), (21, 5), (40, 4)])
+def test_threaded_oracle_equals_single_thread(k, threads):
+    """The threaded CPU baseline (counting split by 8-symbol prefix, mercy by
+    fragment) gives exactly the single-thread oracle's tables."""
+    ascii, offs = synth.random_reads(31 + k, 400, 0, 120, p_invalid=0.01, p_lower=0.1, alphabet=b"ACGT")
+    g_ascii, g_offs = synth.uniform_genome_reads(k, 3000, 600, 80, 0.01)
+    for a, o in ((ascii, offs), (g_ascii, g_offs)):
+        one = oracle.count(a, o, k, 2, mercy=True)
+        many = oracle.count(a, o, k, 2, mercy=True, threads=threads)
+        for key in ("n_kmers", "n_distinct"):
+            assert one[key] == many[key]
+        for key in ("solid_keys", "solid_cnt", "mercy_keys", "mercy_cnt"):
+            assert np.array_equal(one[key], many[key]), key
