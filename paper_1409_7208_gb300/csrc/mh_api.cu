@@ -1,5 +1,6 @@
 // C ABI entry points, context, allocator, profiling and error handling.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <memory>
 
@@ -24,10 +25,24 @@ void cuda_check(cudaError_t e, const char* what) {
     fail(code, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Host-side fault injection for tests: MH_FAULT=alloc:N makes the N-th
+// device allocation of the process (counted from 1, over all contexts) fail
+// as if the device were out of memory; the ones after it succeed.
+static bool injected_alloc_failure() {
+    static const long target = [] {
+        const char* e = std::getenv("MH_FAULT");
+        if (!e || std::strncmp(e, "alloc:", 6) != 0) return 0L;
+        return std::strtol(e + 6, nullptr, 10);
+    }();
+    static std::atomic<long> count{0};
+    return target > 0 && count.fetch_add(1) + 1 == target;
+}
+
 void* ctx_alloc(mh_ctx* ctx, size_t bytes) {
     if (bytes == 0) bytes = 1;
     bytes = (bytes + 255) & ~size_t(255);
     std::lock_guard<std::mutex> lock(ctx->alloc_mu);
+    if (injected_alloc_failure()) fail(MH_ENOMEM, "injected allocation failure (MH_FAULT)");
     if (ctx->budget && ctx->in_use + bytes > ctx->budget)
         fail(MH_ENOMEM, "HBM budget exceeded: " + std::to_string(ctx->in_use) + " + " + std::to_string(bytes) +
                             " > " + std::to_string(ctx->budget) + " bytes");

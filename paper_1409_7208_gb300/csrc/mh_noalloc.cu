@@ -152,7 +152,8 @@ static int sort_noalloc(const uint64_t* in, uint64_t* out, uint64_t n, int key_b
         MH_TRY(cudaMemsetAsync(status, 0, tiles * 256 * sizeof(uint32_t), st));
         MH_TRY(cudaMemsetAsync(counter, 0, sizeof(uint32_t), st));
         onesweep_kernel<NW, false><<<(unsigned)tiles, kSortThreads, smem, st>>>(
-            src, dst, nullptr, nullptr, n, 8 * p, base + (uint64_t)p * 256, nullptr, status, counter, err);
+            src, dst, nullptr, nullptr, n, 8 * p, base + (uint64_t)p * 256, nullptr, status, counter, err,
+            kSpinLimit, 0);
         MH_TRY(cudaGetLastError());
         src = dst;
     }

@@ -13,6 +13,7 @@
 // each with its own look-back chain.  Chunk 0 starts from the global digit
 // offsets of the histogram (the same for every pass); the last tile of chunk
 // c writes the digit offsets where chunk c+1 starts.
+#include <atomic>
 #include <cstdlib>
 #include <vector>
 
@@ -29,6 +30,32 @@ static uint64_t chunk_tiles() {
         return (t >= 1 && t <= kMaxTilesPerChunk) ? t : kMaxTilesPerChunk;
     }();
     return v;
+}
+
+// Polls a look-back wait may make before it gives up (MH_SPIN_LIMIT, >= 1;
+// default kSpinLimit, about a second with the back-off).
+static int spin_limit() {
+    static const int v = [] {
+        const char* e = std::getenv("MH_SPIN_LIMIT");
+        const long x = e ? std::strtol(e, nullptr, 10) : 0;
+        return x >= 1 && x <= kSpinLimit ? (int)x : kSpinLimit;
+    }();
+    return v;
+}
+
+// Test hook: MH_TEST_WITHHOLD_TILE0=N makes the first N scatter launches of
+// the process keep their tile 0 from publishing its counts, so that the
+// bounded waits of the tiles after it run out (MH_ETIMEOUT); later launches
+// are normal.
+static int take_withhold() {
+    static std::atomic<int> left{[] {
+        const char* e = std::getenv("MH_TEST_WITHHOLD_TILE0");
+        return e ? std::atoi(e) : 0;
+    }()};
+    int v = left.load();
+    while (v > 0 && !left.compare_exchange_weak(v, v - 1)) {
+    }
+    return v > 0 ? 1 : 0;
 }
 
 template <int NW, bool HV, int ITEMS, int MINB>
@@ -68,7 +95,7 @@ static bool radix_sort_impl(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t
                         (onesweep_kernel<NW, HV, ITEMS, MINB>), kin + c0 * NW, kout, HV ? vin + c0 : nullptr, vout, len,
                         bit_lo + 8 * p, base.p + ((uint64_t)p * n_chunks + c) * 256,
                         c + 1 < n_chunks ? base.p + ((uint64_t)p * n_chunks + c + 1) * 256 : nullptr, status.p,
-                        counter.p, ctx->d_status);
+                        counter.p, ctx->d_status, spin_limit(), take_withhold());
         }
         std::swap(kin, kout);
         std::swap(vin, vout);

@@ -12,7 +12,7 @@ constexpr uint64_t kMaxTilesPerChunk = (1ull << 18) - 1;
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1;
-constexpr int kSpinLimit = 1 << 23;
+constexpr int kSpinLimit = 1 << 23;  // default bound of a look-back wait (polls)
 
 template <int NW>
 struct SortItems;
@@ -95,7 +95,8 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
     onesweep_kernel(const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout, const uint32_t* __restrict__ vin,
                     uint32_t* __restrict__ vout, uint64_t n, int shift, const uint64_t* __restrict__ digit_base,
                     uint64_t* __restrict__ next_base, uint32_t* __restrict__ status,
-                    uint32_t* __restrict__ tile_counter, uint32_t* __restrict__ err) {
+                    uint32_t* __restrict__ tile_counter, uint32_t* __restrict__ err, int spin_limit,
+                    int withhold_first) {
     constexpr int TILE = sort_tile<NW, ITEMS>();
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* warp_hist = reinterpret_cast<uint32_t*>(smem);          // [warps][256]
@@ -168,9 +169,11 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
         warp_hist[w * 256 + d] = cnt;
         cnt += c;
     }
-    // publish this tile's count early so later tiles can proceed
+    // publish this tile's count early so later tiles can proceed (a test
+    // hook, withhold_first, keeps tile 0 from publishing: the next tiles'
+    // bounded waits then run out and report it)
     uint32_t* st = status + (uint64_t)tile * 256 + d;
-    st_relaxed_u32(st, (tile == 0 ? kFlagInc : kFlagAgg) | cnt);
+    if (!(withhold_first && tile == 0)) st_relaxed_u32(st, (tile == 0 ? kFlagInc : kFlagAgg) | cnt);
     // block exclusive scan of the tile counts -> start of digit d in the tile
     uint32_t start;
     {
@@ -212,7 +215,7 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
             uint32_t s = ld_relaxed_u32(sp);
             int spins = 0;
             while ((s & ~kCountMask) == 0) {
-                if (++spins > kSpinLimit) {
+                if (++spins > spin_limit) {
                     ok = false;
                     break;
                 }
