@@ -381,7 +381,7 @@ BATCHED = {
     "name": "batched: 64 independent read sets, reads per set lognormal (ln-median halfway between 50k and 5M, "
             "sigma a quarter of that span) clipped to [50k, 5M], pairs of 2x150 bp, each set a 10-genome "
             "mini-metagenome (genomes lognormal, median 2 Mbp), 3' error ramp to 1% (mean 0.5%), k=31, d=2, "
-            "mercy on; the whole batch through mh_run_batch on 4 worker streams, tile shape autotuned",
+            "mercy on; the whole batch through mh_run_batch on 4 worker streams, counting plan autotuned",
     "n_sets": 64, "k": 31, "d": 2, "seed": 5, "workers": 4,
 }
 
@@ -448,7 +448,8 @@ def batched_figures(local, n_sets, steps, warmup, workers, seed=None):
     ctx.set_profile(False)
     prof = ctx.profile()
     out = {"sets": len(sets), "reads": n_reads, "bases": n_bases, "k": k, "d": d, "workers": workers,
-           "sort_shape": mh.mh_sort_shape(ctx), "ms": ms, "serial_ms": serial_ms,
+           "sort_shape": mh.mh_sort_shape(ctx), "count_plan": mh.mh_get_count_plan(ctx), "ms": ms,
+           "serial_ms": serial_ms,
            "kmers_per_s": info["n_kmers"] / (ms / 1e3), "serial_kmers_per_s": info["n_kmers"] / (serial_ms / 1e3),
            "jobs_per_s": len(sets) / (ms / 1e3), "serial_jobs_per_s": len(sets) / (serial_ms / 1e3),
            "batch_speedup": serial_ms / ms, "n_kmers": info["n_kmers"], "m": info["m"],
@@ -542,7 +543,7 @@ def run_batched(args, rank, world, local):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                 "config": {"workload": BATCHED["name"], "sets": len(sets), "reads": n_reads, "bases": n_bases,
-                           "k": k, "d": d, "workers": W, "sort_shape": f["sort_shape"],
+                           "k": k, "d": d, "workers": W, "count_plan": f["count_plan"],
                            "l2": "inputs larger than L2 (%.1f GB of reads)" % (n_bases / 1e9)},
                 "serial_value": f["serial_kmers_per_s"], "serial_ms": f["serial_ms"],
                 "batch_speedup": f["batch_speedup"],
@@ -1075,7 +1076,7 @@ def _batched_extra(local, args):
            "sets": f["sets"], "reads": f["reads"], "ms": f["ms"], "serial_ms": f["serial_ms"],
            "jobs_per_s": f["jobs_per_s"], "serial_jobs_per_s": f["serial_jobs_per_s"],
            "kmers_per_s": f["kmers_per_s"], "serial_kmers_per_s": f["serial_kmers_per_s"],
-           "batch_speedup": f["batch_speedup"], "sort_shape": f["sort_shape"]}
+           "batch_speedup": f["batch_speedup"], "count_plan": f["count_plan"]}
     f["ctx"].close()
     del f
     torch.cuda.empty_cache()

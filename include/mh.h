@@ -260,7 +260,7 @@ typedef struct {
 
 #define MH_BATCH_MERCY 1     /* run mh_mercy_kmers on each set */
 #define MH_BATCH_BUILD 2     /* run mh_build_sdbg (solid + mercy) on each set */
-#define MH_BATCH_AUTOTUNE 4  /* time the scatter pass's tile shapes once per context and k */
+#define MH_BATCH_AUTOTUNE 4  /* time counting plans once per context, key width, k and size class */
 
 /* Run the whole path (Sec. 2, paragraphs 1-3: pack, count with the solid
  * filter, mercy, SdBG) on n_sets independent read sets, each an independent
@@ -273,10 +273,12 @@ typedef struct {
  * the call is ordered before every set; ctx's stream waits for every set's
  * last kernel, so work queued on it after the call sees all outputs.  With
  * profiling on, the workers' kernel statistics are added to ctx's.
- * MH_BATCH_AUTOTUNE: before the first batch at a given k of 1-word keys,
- * counts the largest set once with each tile shape of the scatter pass
- * (items per thread x resident CTAs per SM) and keeps the fastest for the
- * context (mh_sort_shape reports it).  Returns MH_OK when every set
+ * MH_BATCH_AUTOTUNE: before the first batch at a given key width, k and size
+ * class (log2 of the largest set's bases, halved), counts the largest set
+ * once with each of a set of counting plans (mh_count_plan: path, scatter
+ * tile shape, unit or spread bits, out-of-core buckets when the set needs
+ * them) and keeps the fastest for the context (mh_get_count_plan reports
+ * it).  Returns MH_OK when every set
  * succeeded, else the first failing set's error (out[i].status tells which).
  * Not to be called concurrently on one context.  Errors: MH_EINVAL (NULL
  * pointers, n_sets < 0, workers outside 1..64, k or d out of range). */
@@ -287,6 +289,32 @@ int mh_run_batch(mh_ctx* ctx, const mh_read_set* sets, int n_sets, int k, int d,
  * a thread at 4 CTAs per SM (the default), 1 = 14 at 3, 2 = 12 at 3; -1
  * before any autotuning (the default applies). */
 int mh_sort_shape(const mh_ctx* ctx);
+
+/* How the context counts (Sec. 2, third paragraph: the sort and count of
+ * every (k+1)-mer).  Every plan gives the same results; only the route and
+ * its speed change.  -1 / 0 fields mean the library's default.
+ *   path              0: unit counting (1-word keys: 8-bit passes over the
+ *                     top bits of the mixed keys, then each unit of about 160
+ *                     keys sorted and counted by one warp); 1: the spread
+ *                     sort (passes over the top ceil(log2 n) bits, a fix-up of
+ *                     keys sharing them, a run pass); wider keys always take 1
+ *   sort_shape        the scatter tile shape (see mh_sort_shape)
+ *   unit_bits_delta   added to the unit bits of path 0 (-2..2)
+ *   spread_bits_delta added to the bits path 1 sorts by passes (-8, 0, 8)
+ *   bucket_bits       out-of-core buckets: 2^bucket_bits (0..6), -1 = the
+ *                     memory plan's choice
+ * MH_BATCH_AUTOTUNE tries a set of plans on the largest set of a batch (per
+ * key width, k and size class of that set) and keeps the fastest.
+ * Errors: MH_EINVAL (NULL, a field out of range). */
+typedef struct {
+    int path;
+    int sort_shape;
+    int unit_bits_delta;
+    int spread_bits_delta;
+    int bucket_bits;
+} mh_count_plan;
+int mh_get_count_plan(const mh_ctx* ctx, mh_count_plan* out);
+int mh_set_count_plan(mh_ctx* ctx, const mh_count_plan* plan);
 
 /* ------------------------------------------------- no-allocation sort */
 

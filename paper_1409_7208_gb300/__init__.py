@@ -35,7 +35,8 @@ SYMBOLS = (
     "mh_sdbg_view_get", "mh_free_sdbg", "mh_strerror", "mh_last_error_message", "mh_stream",
     "mh_memory", "mh_profile_count", "mh_profile_get", "mh_profile_reset", "mh_set_profile",
     "mh_sort_keys_noalloc", "mh_walk_contigs", "mh_contigs_view_get", "mh_free_contigs",
-    "mh_pack_reads_contigs", "mh_trim", "mh_run_batch", "mh_sort_shape",
+    "mh_pack_reads_contigs", "mh_trim", "mh_run_batch", "mh_sort_shape", "mh_get_count_plan",
+    "mh_set_count_plan",
 )
 
 MH_BATCH_MERCY, MH_BATCH_BUILD, MH_BATCH_AUTOTUNE = 1, 2, 4
@@ -137,6 +138,8 @@ def load_library(path: str = LIB_PATH):
     lib.mh_run_batch.argtypes = [P, ctypes.POINTER(ReadSet), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int, ctypes.POINTER(SetResult)]
     lib.mh_sort_shape.argtypes = [P]
+    lib.mh_get_count_plan.argtypes = [P, ctypes.POINTER(CountPlan)]
+    lib.mh_set_count_plan.argtypes = [P, ctypes.POINTER(CountPlan)]
     _lib = lib
     return lib
 
@@ -507,6 +510,28 @@ def mh_run_batch(ctx: Context, sets, k: int, d: int = 2, workers: int = 4, mercy
                     o[key].free()
         ctx._check(rc)
     return out
+
+
+PLAN_FIELDS = ("path", "sort_shape", "unit_bits_delta", "spread_bits_delta", "bucket_bits")
+
+
+class CountPlan(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int) for f in PLAN_FIELDS]
+
+
+def mh_get_count_plan(ctx: Context) -> dict:
+    """The context's counting plan (mh_count_plan) as a dict."""
+    p = CountPlan()
+    ctx._check(ctx._lib.mh_get_count_plan(ctx._h, ctypes.byref(p)))
+    return {f: getattr(p, f) for f in PLAN_FIELDS}
+
+
+def mh_set_count_plan(ctx: Context, **fields) -> None:
+    """Set the context's counting plan; fields not given keep their value."""
+    cur = mh_get_count_plan(ctx)
+    cur.update(fields)
+    p = CountPlan(*[int(cur[f]) for f in PLAN_FIELDS])
+    ctx._check(ctx._lib.mh_set_count_plan(ctx._h, ctypes.byref(p)))
 
 
 def mh_sort_shape(ctx: Context) -> int:

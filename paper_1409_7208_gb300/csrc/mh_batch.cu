@@ -11,9 +11,10 @@
 // that sizes an output, the other streams keep the SMs busy, and a small
 // set's short kernels run beside a large set's.
 //
-// The autotuner times the scatter pass's tile shapes on the largest set of
-// the first batch at a k with 1-word keys and keeps the fastest for the
-// context.
+// The autotuner counts the largest set of the first batch at a key width, k
+// and size class once with each of a set of counting plans (route, scatter
+// tile shape, unit or spread bits, out-of-core buckets when the set needs
+// them) and keeps the fastest for the context.
 #include <algorithm>
 #include <condition_variable>
 #include <mutex>
@@ -63,17 +64,54 @@ int run_job(mh_ctx* w, const mh_read_set& s, int k, int d, int flags, mh_set_res
     return rc;
 }
 
-// Count `s` once per tile shape on worker w (after one untimed count) and
-// return the fastest shape.
-int tune_shape(mh_ctx* w, const mh_read_set& s, int k, int d) {
+using Plan = std::vector<int>;  // path, sort_shape, unit_bits_delta, spread_bits_delta, bucket_bits
+
+void apply_plan(mh_ctx* w, const Plan& p) {
+    w->count_path = p[0];
+    w->sort_shape = p[1];
+    w->unit_bits_delta = p[2];
+    w->spread_bits_delta = p[3];
+    w->bucket_bits = p[4];
+}
+
+// The plans tried for a set: for 1-word keys the unit counting with each
+// tile shape and unit bits one either side, and the spread route with its
+// bits one digit either side; for wider keys the spread bits; and, when the
+// memory plan splits the set into buckets, one bucket bit more.
+std::vector<Plan> candidate_plans(int nw, int auto_buckets) {
+    std::vector<Plan> c;
+    if (nw == 1) {
+        for (int shape = 0; shape < kSortShapes; shape++) c.push_back({0, shape, 0, 0, -1});
+        c.push_back({0, 0, -1, 0, -1});
+        c.push_back({0, 0, 1, 0, -1});
+        for (int sb : {0, 8, -8}) c.push_back({1, 0, 0, sb, -1});
+    } else {
+        for (int sb : {0, 8, -8}) c.push_back({1, 0, 0, sb, -1});
+    }
+    if (auto_buckets > 0 && auto_buckets < 6) {
+        Plan p = c[0];
+        p[4] = auto_buckets + 1;
+        c.push_back(p);
+    }
+    return c;
+}
+
+// Count `s` on worker w once untimed, then once per candidate plan, and
+// return the fastest plan (empty if a count failed).
+Plan tune_plan(mh_ctx* w, const mh_read_set& s, int k, int d) {
     mh_reads* reads = nullptr;
-    if (mh_pack_reads(w, s.ascii, s.n_bases, s.offs, s.n_reads, s.on_device, &reads) != MH_OK) return -1;
+    if (mh_pack_reads(w, s.ascii, s.n_bases, s.offs, s.n_reads, s.on_device, &reads) != MH_OK) return {};
     cudaEvent_t a = nullptr, b = nullptr;
-    int best = -1;
+    Plan best;
     float best_ms = 0.f;
+    const Plan keep = {w->count_path, w->sort_shape, w->unit_bits_delta, w->spread_bits_delta, w->bucket_bits};
     if (cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess) {
-        for (int shape = -1; shape < kSortShapes; shape++) {
-            w->sort_shape = shape < 0 ? 0 : shape;
+        const int nw = words_for(k);
+        const uint64_t kk = (uint64_t)k * s.n_reads;
+        w->bucket_bits = -1;
+        std::vector<Plan> cands = candidate_plans(nw, count_bucket_bits(w, s.n_bases > kk ? s.n_bases - kk : 0, nw));
+        for (size_t i = 0; i <= cands.size(); i++) {
+            apply_plan(w, i == 0 ? cands[0] : cands[i - 1]);  // the first count warms up
             mh_kmers* solid = nullptr;
             cudaEventRecord(a, w->stream);
             const int rc = mh_count_kmers(w, reads, k, d, &solid);
@@ -83,15 +121,16 @@ int tune_shape(mh_ctx* w, const mh_read_set& s, int k, int d) {
             cudaEventElapsedTime(&ms, a, b);
             mh_free_kmers(solid);
             if (rc != MH_OK) {
-                best = -1;
+                best.clear();
                 break;
             }
-            if (shape >= 0 && (best < 0 || ms < best_ms)) {
-                best = shape;
+            if (i > 0 && (best.empty() || ms < best_ms)) {
+                best = cands[i - 1];
                 best_ms = ms;
             }
         }
     }
+    apply_plan(w, keep);
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
     mh_free_reads(reads);
@@ -103,6 +142,25 @@ int tune_shape(mh_ctx* w, const mh_read_set& s, int k, int d) {
 extern "C" {
 
 int mh_sort_shape(const mh_ctx* ctx) { return ctx ? ctx->sort_shape : -1; }
+
+int mh_get_count_plan(const mh_ctx* ctx, mh_count_plan* out) {
+    if (!ctx || !out) return MH_EINVAL;
+    *out = mh_count_plan{ctx->count_path, ctx->sort_shape, ctx->unit_bits_delta, ctx->spread_bits_delta,
+                         ctx->bucket_bits};
+    return MH_OK;
+}
+
+int mh_set_count_plan(mh_ctx* ctx, const mh_count_plan* p) {
+    if (!ctx || !p || p->path < -1 || p->path > 1 || p->sort_shape < -1 || p->sort_shape >= kSortShapes ||
+        p->unit_bits_delta < -2 || p->unit_bits_delta > 2 ||
+        (p->spread_bits_delta != 0 && p->spread_bits_delta != 8 && p->spread_bits_delta != -8) ||
+        p->bucket_bits < -1 || p->bucket_bits > 6) {
+        if (ctx) ctx->last_error = "mh_set_count_plan: a field out of range";
+        return MH_EINVAL;
+    }
+    apply_plan(ctx, {p->path, p->sort_shape, p->unit_bits_delta, p->spread_bits_delta, p->bucket_bits});
+    return MH_OK;
+}
 
 int mh_run_batch(mh_ctx* ctx, const mh_read_set* sets, int n_sets, int k, int d, int workers, int flags,
                  mh_set_result* out) {
@@ -141,14 +199,21 @@ int mh_run_batch(mh_ctx* ctx, const mh_read_set* sets, int n_sets, int k, int d,
         std::iota(order.begin(), order.end(), 0);
         std::stable_sort(order.begin(), order.end(),
                          [&](int a, int b) { return sets[a].n_bases > sets[b].n_bases; });
-        if ((flags & MH_BATCH_AUTOTUNE) && words_for(k) == 1 && ctx->tuned_k != k) {
-            const int shape = tune_shape(ctx->workers[0], sets[order[0]], k, d);
-            if (shape >= 0) {
-                ctx->sort_shape = shape;
-                ctx->tuned_k = k;
+        if (flags & MH_BATCH_AUTOTUNE) {
+            const mh_read_set& big = sets[order[0]];
+            int cls = 0;
+            while (cls < 63 && (2ull << cls) <= big.n_bases) cls++;
+            const auto key = std::make_tuple(words_for(k), k, cls / 2);
+            auto it = ctx->tuned.find(key);
+            if (it == ctx->tuned.end()) {
+                const Plan p = tune_plan(ctx->workers[0], big, k, d);
+                if (!p.empty()) it = ctx->tuned.emplace(key, p).first;
             }
+            if (it != ctx->tuned.end()) apply_plan(ctx, it->second);
         }
-        for (int i = 0; i < workers; i++) ctx->workers[i]->sort_shape = ctx->sort_shape;
+        for (int i = 0; i < workers; i++)
+            apply_plan(ctx->workers[i], {ctx->count_path, ctx->sort_shape, ctx->unit_bits_delta,
+                                         ctx->spread_bits_delta, ctx->bucket_bits});
 
         const uint64_t plan = ctx->budget ? ctx->budget : ctx->device_bytes / 20 * 17;
         const uint64_t budget = plan > ctx->in_use ? plan - ctx->in_use : 0;

@@ -661,13 +661,14 @@ template void expand_runs<4>(mh_ctx*, const uint64_t*, uint64_t, int, int, Buf<u
 // window) fits in 90% of it; otherwise enough buckets (up to 64) that one
 // bucket's working set and the byte a window of bucket numbers take at most
 // 60% of it.  MH_COUNT_BUCKET_BITS (0..6) forces the number (tests).
-static int count_bucket_bits(mh_ctx* ctx, uint64_t n, int nw) {
+int count_bucket_bits(mh_ctx* ctx, uint64_t n, int nw) {
     static const int forced = [] {
         const char* e = std::getenv("MH_COUNT_BUCKET_BITS");
         const int v = e ? std::atoi(e) : -1;
         return v >= 0 && v <= 6 ? v : -1;
     }();
     if (forced >= 0) return forced;
+    if (ctx->bucket_bits >= 0) return ctx->bucket_bits;
     if (!n) return 0;
     const double per = 24.0 * nw + 12.0;
     const uint64_t budget = ctx->budget ? ctx->budget : ctx->device_bytes / 20 * 17;
@@ -682,15 +683,16 @@ static int count_bucket_bits(mh_ctx* ctx, uint64_t n, int nw) {
     return bb;
 }
 
-// The unit counting (wide-digit passes, units sorted and counted on chip)
-// for 1-word keys, unless MH_COUNT_PATH=spread selects the 8-bit spread sort
-// with the fix-up and the run pass (A/B runs and tests).
-static bool use_unit_count() {
+// The unit counting (8-bit passes over the top bits, units sorted and
+// counted by a warp each) for 1-word keys, unless the context's plan or
+// MH_COUNT_PATH=spread selects the spread sort with the fix-up and the run
+// pass.
+static bool use_unit_count(const mh_ctx* ctx) {
     static const bool v = [] {
         const char* e = std::getenv("MH_COUNT_PATH");
         return !(e && std::string(e) == "spread");
     }();
-    return v;
+    return ctx->count_path >= 0 ? ctx->count_path == 0 : v;
 }
 
 template <int NW>
@@ -713,8 +715,8 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
     out->n_kmers = 2 * n;
     out->spectrum_mixed = kMixed;
     const int bb = count_bucket_bits(ctx, n, NW);
-    const GroupPlan gp = group_plan(n, 0);
-    if (bb == 0 && NW == 1 && use_unit_count() && gp.passes >= 0) {
+    const GroupPlan gp = group_plan(ctx, n, 0);
+    if (bb == 0 && NW == 1 && use_unit_count(ctx) && gp.passes >= 0) {
         // 1-word keys: 8-bit passes over the top bits, then the units sorted
         // and counted by a warp each (mh_group.cu)
         Buf<uint64_t> keys(ctx, n ? n : 1), alt(ctx, n ? n : 1);
@@ -750,7 +752,7 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
         Buf<uint64_t> keys(ctx, (n ? n : 1) * NW), alt(ctx, (n ? n : 1) * NW);
         // the extraction counts the digits of the spread sort's passes (1-word
         // keys: for wider keys it measured no faster than the histogram pass)
-        const int P = spread_pass_bits(n);
+        const int P = spread_pass_bits(ctx, n);
         const bool fuse = NW == 1 && n > 1 && P < 64;
         const int n_passes = (P + 7) / 8;
         Buf<uint32_t> hist(ctx, fuse ? (size_t)n_passes * 256 : 1);
@@ -827,8 +829,8 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
         Buf<uint32_t> sc;
         uint64_t S = 0, runs = 0, palins = 0;
         RunList list;
-        const GroupPlan bp = group_plan(m, bb);
-        if (NW == 1 && use_unit_count() && bp.passes >= 0) {
+        const GroupPlan bp = group_plan(ctx, m, bb);
+        if (NW == 1 && use_unit_count(ctx) && bp.passes >= 0) {
             const bool in_alt = bp.passes ? radix_sort<1>(ctx, keys.p, alt.p, nullptr, nullptr, m,
                                                           64 - bb - 8 * bp.passes, 64 - bb)
                                           : false;

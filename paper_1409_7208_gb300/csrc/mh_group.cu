@@ -36,6 +36,7 @@
 // with more than 32 distinct ones (neither is met with mixed keys, but both
 // are possible for skewed input), is set aside: it is sorted afterwards by
 // the general radix sort and its runs counted from the sorted keys.
+#include <algorithm>
 #include <cstdlib>
 #include <vector>
 
@@ -567,8 +568,9 @@ static int env_int(const char* name, int dflt) {
 }
 
 // MH_GROUP_UNIT_BITS (0..30) forces the unit bits; tests use it for one
-// unit or many small ones.
-GroupPlan group_plan(uint64_t n, int skip) {
+// unit or many small ones.  Otherwise the fewest bits that leave about
+// kUnitTarget keys a unit, moved by the context's plan.
+GroupPlan group_plan(mh_ctx* ctx, uint64_t n, int skip) {
     static const int forced = env_int("MH_GROUP_UNIT_BITS", -1);
     GroupPlan p;
     int ub = 0;
@@ -576,6 +578,7 @@ GroupPlan group_plan(uint64_t n, int skip) {
         ub = forced;
     } else {
         while (ub < 30 && ceil_div(n, 1ull << ub) > kUnitTarget) ub++;
+        if (ub > 0 && ctx) ub = std::max(1, std::min(30, ub + ctx->unit_bits_delta));
     }
     p.unit_bits = ub;
     p.passes = (ub + 7) / 8;

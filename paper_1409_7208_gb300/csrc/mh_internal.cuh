@@ -10,7 +10,9 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <unordered_map>
 #include <utility>
@@ -54,7 +56,12 @@ struct mh_ctx {
     cudaEvent_t pack_ev[5] = {};         // the staged upload's events (created on first use)
     std::vector<mh_ctx*> workers;        // worker contexts of mh_run_batch (created on first use)
     int sort_shape = -1;                 // scatter tile shape for 1-word keys (-1: default)
-    int tuned_k = -1;                    // k the shape was tuned at
+    // the counting plan (mh_set_count_plan, or the batch autotuner); defaults: -1 / 0
+    int count_path = -1;                 // 0: unit counting (1-word keys), 1: spread sort, fix-up, run pass
+    int unit_bits_delta = 0;             // added to the unit bits of the unit counting
+    int spread_bits_delta = 0;           // added to the bits the count's spread passes cover (x 8)
+    int bucket_bits = -1;                // out-of-core buckets (0..6); -1: the memory plan's choice
+    std::map<std::tuple<int, int, int>, std::vector<int>> tuned;  // (nw, k, size class) -> plan
     uint64_t device_bytes = 0;           // the device's memory, for plans when no budget is set
     mh_alloc_fn alloc = nullptr;
     mh_free_fn free_fn = nullptr;
@@ -620,7 +627,7 @@ bool radix_sort(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint
 // key), then a fix-up of the keys that share them.  `hist`: the counts of
 // those passes' digits (as for radix_sort), or nullptr.  Returns true if the
 // result is in alt.
-int spread_pass_bits(uint64_t n);
+int spread_pass_bits(mh_ctx* ctx, uint64_t n);
 template <int NW>
 bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n, int skip = 0,
                        const uint32_t* hist = nullptr);
@@ -665,6 +672,10 @@ struct RunList {
     uint64_t n = 0;
 };
 
+// Out-of-core buckets of the count of n canonical windows of nw-word keys:
+// 0 (all in memory) or bits of 2^bits buckets (mh_count.cu).
+int count_bucket_bits(mh_ctx* ctx, uint64_t n, int nw);
+
 // How the unit counting splits n 1-word keys whose top `skip` bits are
 // equal: units of the next unit_bits bits (about 100-160 keys each), sorted
 // into place by `passes` 8-bit LSD passes over the next 8 * passes bits.
@@ -673,7 +684,7 @@ struct GroupPlan {
     int unit_bits = 0;
     int passes = 0;
 };
-GroupPlan group_plan(uint64_t n, int skip);
+GroupPlan group_plan(mh_ctx* ctx, uint64_t n, int skip);
 
 // Unit counting of mixed canonical 1-word keys (defined in mh_group.cu):
 // `sorted` holds n keys sorted by their top skip + 8 * plan.passes bits,

@@ -655,12 +655,17 @@ static int spread_bits(uint64_t n) {
     return forced ? forced : std::max(8, ((ceil_log2(n) + 7) / 8) * 8);
 }
 
-int spread_pass_bits(uint64_t n) { return spread_bits(n); }
+// The count sort's spread bits: the default moved by the context's plan
+// (a multiple of 8, kept in [8, 64]).
+int spread_pass_bits(mh_ctx* ctx, uint64_t n) {
+    const int P = spread_bits(n) + (ctx ? ctx->spread_bits_delta : 0);
+    return std::min(64, std::max(8, P / 8 * 8));
+}
 
 template <int NW>
 bool radix_sort_spread(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n, int skip, const uint32_t* hist) {
     using F = Fix<NW>;
-    const int P = spread_bits(n);
+    const int P = spread_pass_bits(ctx, n);
     const int bits = 64 * NW;
     if (n <= 1 || P + skip >= 64) return radix_sort<NW>(ctx, keys, alt, nullptr, nullptr, n, 0, bits - skip);
     // the top `skip` bits are equal in every key: passes over the P bits below

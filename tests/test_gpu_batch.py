@@ -106,3 +106,70 @@ def test_batch_reports_a_failing_set(mh):
     assert e.value.code == mh.MH_EINVAL
     assert mh.mh_run_batch(ctx, [], 31, 2) == []
     ctx.close()
+
+
+def _plans(nw):
+    """The counting plans the batch autotuner tries (mh_batch.cu), plus
+    forced out-of-core bucket counts."""
+    p = []
+    if nw == 1:
+        p += [dict(path=0, sort_shape=s, unit_bits_delta=0, spread_bits_delta=0) for s in range(3)]
+        p += [dict(path=0, sort_shape=0, unit_bits_delta=u, spread_bits_delta=0) for u in (-1, 1)]
+    p += [dict(path=1, sort_shape=0, unit_bits_delta=0, spread_bits_delta=b) for b in (0, 8, -8)]
+    return p + [dict(p[0], bucket_bits=1), dict(p[0], bucket_bits=3)]
+
+
+@pytest.mark.parametrize("k", [31, 47])
+def test_every_counting_plan_gives_the_same_outputs(mh, k):
+    """Each plan the autotuner may pick (route, tile shape, unit or spread
+    bits, bucket count) yields outputs bit-identical to the default plan's."""
+    a, o = synth.uniform_genome_reads(61, 200_000, 40_000, 150, 0.01)
+    ctx = mh.Context(device=0)
+    want = _plain(mh, ctx, a, o, k, 2)
+    for plan in _plans(1 if k <= 31 else 2):
+        mh.mh_set_count_plan(ctx, **dict(dict(bucket_bits=-1), **plan))
+        assert mh.mh_get_count_plan(ctx)["path"] == plan["path"]
+        got = _plain(mh, ctx, a, o, k, 2)
+        for i, part in enumerate(("keys", "counts")):
+            assert np.array_equal(got[0][part], want[0][part]), (plan, part)
+            assert np.array_equal(got[1][part], want[1][part]), (plan, part)
+        for key in ("W", "last", "dummy", "F", "aux"):
+            assert np.array_equal(got[2][key], want[2][key]), (plan, key)
+    with pytest.raises(mh.MhError):
+        mh.mh_set_count_plan(ctx, spread_bits_delta=4)
+
+
+def test_autotuned_plan_is_no_slower_than_the_default(mh):
+    """The plan the batch autotuner keeps counts the tuning set no slower
+    than the default plan (best of five each, 15% allowed for noise)."""
+    import time
+
+    import torch
+    sets = [synth.uniform_genome_reads(70 + i, 2_000_000, 400_000 - 50_000 * i, 150, 0.005) for i in range(4)]
+    dev = [(torch.from_numpy(a).cuda(), torch.from_numpy(o.view(np.int64)).cuda()) for a, o in sets]
+    ctx = mh.Context(device=0)
+    res = mh.mh_run_batch(ctx, dev, 31, 2, workers=2, autotune=True)
+    for r in res:
+        for key in ("sdbg", "mercy", "solid"):
+            r[key].free()
+    tuned = mh.mh_get_count_plan(ctx)
+    assert tuned["path"] in (0, 1)
+
+    def best(plan):
+        c = mh.Context(device=0)
+        mh.mh_set_count_plan(c, **plan)
+        reads = mh.mh_pack_reads(c, *dev[0])
+        times = []
+        for _ in range(6):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s = mh.mh_count_kmers(c, reads, 31, 2)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            s.free()
+        del reads
+        c.close()
+        return min(times[1:])
+
+    default = dict(path=-1, sort_shape=-1, unit_bits_delta=0, spread_bits_delta=0, bucket_bits=-1)
+    assert best(tuned) <= 1.15 * best(default), tuned
