@@ -629,12 +629,8 @@ void expand_runs(mh_ctx* ctx, const uint64_t* sorted, uint64_t n, int k, int d, 
     big_k.reset();
     big_c.reset();
     // the table's keys are distinct and, as (k+1)-mers of both strands, their
-    // top bits spread: the spread order with counts attached (1-word keys)
-    bool in_alt;
-    if constexpr (NW == 1)
-        in_alt = radix_sort_spread_kv<1>(ctx, keys.p, alt.p, cnt.p, calt.p, S, 64 - 2 * K1);
-    else
-        in_alt = radix_sort<NW>(ctx, keys.p, alt.p, cnt.p, calt.p, S, 0, 2 * K1);
+    // top bits spread: the spread order with counts attached
+    const bool in_alt = radix_sort_spread_kv<NW>(ctx, keys.p, alt.p, cnt.p, calt.p, S, 64 * NW - 2 * K1);
     if (in_alt) {
         out_keys = std::move(alt);
         out_cnt = std::move(calt);

@@ -52,6 +52,7 @@ constexpr int kWarpCap = 512;                 // keys a warp sorts on chip
 constexpr int kSubBits = 8;
 constexpr int kSubBuckets = 1 << kSubBits;
 constexpr uint64_t kUnitTarget = 160;         // most keys an average unit holds
+constexpr uint64_t kUnitMax = 256;            // ... when that saves a pass
 constexpr uint32_t kTileKeys = 4096;          // keys a warp's tile holds
 constexpr uint64_t kMaxRounds = 64;           // runs of a large unit counted from global memory
 
@@ -578,6 +579,9 @@ GroupPlan group_plan(mh_ctx* ctx, uint64_t n, int skip) {
         ub = forced;
     } else {
         while (ub < 30 && ceil_div(n, 1ull << ub) > kUnitTarget) ub++;
+        // one bit past a whole number of passes costs a whole pass: units of
+        // up to kUnitMax keys on average are cheaper than that pass
+        if (ub % 8 == 1 && ceil_div(n, 1ull << (ub - 1)) <= kUnitMax) ub--;
         if (ub > 0 && ctx) ub = std::max(1, std::min(30, ub + ctx->unit_bits_delta));
     }
     p.unit_bits = ub;

@@ -440,6 +440,21 @@ __global__ void __launch_bounds__(256) spread_big_kernel(uint64_t* __restrict__ 
     }
 }
 
+// a and b agree on every bit at or above bit lo of the whole key (bit 0 the
+// lowest bit of word 0).
+template <int NW>
+__device__ __forceinline__ bool same_above(const Key<NW>& a, const Key<NW>& b, int lo) {
+    bool eq = true;
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+        const int b0 = 64 * w;
+        if (lo >= b0 + 64) continue;
+        const uint64_t x = a.w[w] ^ b.w[w];
+        eq &= (lo <= b0) ? x == 0 : (x >> (lo - b0)) == 0;
+    }
+    return eq;
+}
+
 // Key-value fix-up (keys with a 32-bit payload): groups of up to 16 keys
 // are sorted by one thread each, pairs moving together; larger groups inside
 // the window by one warp (successive minima: each round writes every copy
@@ -475,14 +490,13 @@ __global__ void __launch_bounds__(256) spread_fix_kv_kernel(uint64_t* __restrict
     for (uint32_t i = tid; i < W; i += 256) V[i] = vals[s + i];
     if (tid == 0) n_queue = 0;
     __syncthreads();
-    const uint64_t same_top = 1ull << lo;
     for (uint32_t wd = warp; wd < (uint32_t)F::kWords; wd += 8) {
         const uint32_t i = wd * 32 + lane;
         bool h = false, d = false;
         if (i < W) {
             const Key<NW> x = kget(i);
             const Key<NW> y = i > 0 ? kget(i - 1) : (s > 0 ? load_key<NW>(keys, s - 1) : key_ones<NW>());
-            h = i == 0 && s == 0 ? true : (x.w[NW - 1] ^ y.w[NW - 1]) >= same_top;
+            h = i == 0 && s == 0 ? true : !same_above<NW>(x, y, lo);
             d = i > 0 && !h && key_less<NW>(x, y);
         }
         const uint32_t hb = __ballot_sync(0xFFFFFFFFu, h), db = __ballot_sync(0xFFFFFFFFu, d);
@@ -593,8 +607,8 @@ __global__ void __launch_bounds__(256) spread_fix_kv_kernel(uint64_t* __restrict
     }
 }
 
-// A CTA per listed group start: the group's end (first key with other top
-// bits), and (start, end) out if the group holds a descent.
+// A CTA per listed group start: the group's end (the first key differing at
+// or above bit lo), and (start, end) out if the group holds a descent.
 template <int NW>
 __global__ void __launch_bounds__(256) spread_bounds_kernel(const uint64_t* __restrict__ keys, uint64_t n, int lo,
                                                             const uint64_t* __restrict__ list, uint64_t n_list,
@@ -602,11 +616,10 @@ __global__ void __launch_bounds__(256) spread_bounds_kernel(const uint64_t* __re
                                                             unsigned long long* __restrict__ n_rest) {
     __shared__ uint64_t s_end;
     const int tid = threadIdx.x;
-    auto top = [&](uint64_t i) { return keys[i * NW + NW - 1] >> lo; };
     for (uint64_t g = blockIdx.x; g < n_list; g += gridDim.x) {
         const uint64_t gs = list[g];
         if (tid == 0) {
-            const uint64_t px = top(gs);
+            const Key<NW> px = load_key<NW>(keys, gs);
             uint64_t l = gs + 1, step = 1, h;
             while (true) {
                 const uint64_t probe = l + step - 1;
@@ -614,7 +627,7 @@ __global__ void __launch_bounds__(256) spread_bounds_kernel(const uint64_t* __re
                     h = n;
                     break;
                 }
-                if (top(probe) != px) {
+                if (!same_above<NW>(load_key<NW>(keys, probe), px, lo)) {
                     h = probe;
                     break;
                 }
@@ -623,7 +636,7 @@ __global__ void __launch_bounds__(256) spread_bounds_kernel(const uint64_t* __re
             }
             while (l < h) {
                 const uint64_t mid = (l + h) / 2;
-                if (top(mid) == px) l = mid + 1; else h = mid;
+                if (same_above<NW>(load_key<NW>(keys, mid), px, lo)) l = mid + 1; else h = mid;
             }
             s_end = l;
         }
@@ -724,9 +737,9 @@ bool radix_sort_spread_kv(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* 
         const char* e = std::getenv("MH_SPREAD_KV_MIN");
         return e ? (uint64_t)std::strtoull(e, nullptr, 10) : (uint64_t)1 << 20;
     }();
-    if (n < std::max<uint64_t>(kv_min, 2) || P + skip >= 64)
+    if (n < std::max<uint64_t>(kv_min, 2) || P + skip >= bits)
         return radix_sort<NW>(ctx, keys, alt, vals, valt, n, 0, bits - skip);
-    const int lo = 64 - skip - P;
+    const int lo = bits - skip - P;  // groups: keys equal at and above bit lo of the whole key
     const bool in_alt = radix_sort<NW>(ctx, keys, alt, vals, valt, n, bits - skip - P, bits - skip);
     uint64_t* k = in_alt ? alt : keys;
     uint64_t* ko = in_alt ? keys : alt;
@@ -762,6 +775,8 @@ bool radix_sort_spread_kv(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* 
 }
 
 template bool radix_sort_spread_kv<1>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*, uint64_t, int);
+template bool radix_sort_spread_kv<2>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*, uint64_t, int);
+template bool radix_sort_spread_kv<4>(mh_ctx*, uint64_t*, uint64_t*, uint32_t*, uint32_t*, uint64_t, int);
 
 template bool radix_sort_spread<1>(mh_ctx*, uint64_t*, uint64_t*, uint64_t, int, const uint32_t*);
 template bool radix_sort_spread<2>(mh_ctx*, uint64_t*, uint64_t*, uint64_t, int, const uint32_t*);
