@@ -232,7 +232,9 @@ def cpu_baseline_pair(ascii, offs, k, d, sample):
 
 
 def run_reference(args, wl, rank, world):
-    """The CPU oracle as it stands, one thread, on the bounded sample."""
+    """The CPU oracle as it stands, on the bounded sample: counting and mercy
+    split over every host core (the threaded form, equal to the one-thread
+    oracle by test), the SdBG build on one."""
     if rank != 0:
         return
     ascii, offs = wl["sample"](wl["seed"], CPU_SAMPLE_READS)
