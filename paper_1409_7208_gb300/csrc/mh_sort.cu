@@ -4,11 +4,12 @@
 // Sort: one histogram kernel counts every 8-bit digit of every pass in a
 // single read of the keys; then each pass is one "onesweep" kernel: a CTA
 // takes the next tile (dynamic tile id, so every earlier tile already runs),
-// ranks its keys by digit with warp match/ballot and shared-memory warp
-// histograms (stable: rank follows input order), publishes its per-digit
-// counts, looks back over earlier tiles' published counts (decoupled
-// look-back, every wait bounded), stages the tile in shared memory in digit
-// order and writes it out in coalesced runs.  Look-back counts are 30-bit,
+// counts its keys' digits in per-warp shared-memory histograms, publishes
+// the tile's per-digit counts, ranks the keys by digit with warp match and
+// one shared atomic per group of equal digits (stable: rank follows input
+// order) while staging them in shared memory in digit order, looks back
+// over earlier tiles' published counts (decoupled look-back, every wait
+// bounded) and writes the tile out in coalesced runs.  Look-back counts are 30-bit,
 // so a pass runs in chunks of at most (2^18 - 1) tiles, one launch per chunk,
 // each with its own look-back chain.  Chunk 0 starts from the global digit
 // offsets of the histogram (the same for every pass); the last tile of chunk
@@ -104,10 +105,10 @@ static bool radix_sort_impl(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t
 }
 
 // Tile shape of the scatter pass for 1-word keys: (items per thread,
-// resident CTAs per SM).  The defaults, (12, 4) for keys alone and (12, 3)
-// with a payload (which needs more than 64 registers), measured fastest on
-// GB300; a context's tuned shape (mh_run_batch's autotuner) or
-// MH_SORT_VARIANT selects another key-only shape.
+// resident CTAs per SM).  The defaults, (16, 3) for keys alone and (14, 3)
+// with a payload, measured fastest on GB300; a context's tuned shape
+// (mh_run_batch's autotuner) or MH_SORT_VARIANT selects another key-only
+// shape: 1 = (12, 4), 2 = (14, 3).
 static int sort_variant() {
     static int v = [] {
         const char* e = std::getenv("MH_SORT_VARIANT");
@@ -121,12 +122,12 @@ static bool radix_sort_dispatch(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint
                                 uint64_t n, int bit_lo, int bit_hi, const uint32_t* h) {
     if constexpr (NW == 1) {
         if constexpr (HV) {
-            return radix_sort_impl<NW, HV, 12, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h);
+            return radix_sort_impl<NW, HV, 14, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h);
         } else {
             switch (ctx->sort_shape >= 0 ? ctx->sort_shape : sort_variant()) {
-                case 1: return radix_sort_impl<NW, HV, 14, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h);
-                case 2: return radix_sort_impl<NW, HV, 12, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h);
-                default: return radix_sort_impl<NW, HV, 12, 4>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h);
+                case 1: return radix_sort_impl<NW, HV, 12, 4>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h);
+                case 2: return radix_sort_impl<NW, HV, 14, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h);
+                default: return radix_sort_impl<NW, HV, 16, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h);
             }
         }
     }

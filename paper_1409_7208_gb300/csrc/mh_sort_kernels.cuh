@@ -22,7 +22,7 @@ struct SortItems<1> {
 };
 template <>
 struct SortItems<2> {
-    static constexpr int v = 10;
+    static constexpr int v = 12;
 };
 template <>
 struct SortItems<4> {
@@ -120,7 +120,6 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
     // load: warp-striped, item i of lane l is tile key warp*32*ITEMS + 32*i + l
     Key<NW> k[ITEMS];
     uint32_t v[HV ? ITEMS : 1];
-    uint32_t rd[ITEMS];  // (rank within warp << 8) | digit
     const uint32_t w0 = (uint32_t)warp * 32 * ITEMS + lane;
     if (full) {
 #pragma unroll
@@ -141,24 +140,12 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
             }
         }
     }
-    // rank within the warp, stable by item then lane: every lane of a group
-    // of equal digits reads the warp's counter, then the group's first lane
-    // adds the group size (the histogram is the warp's own, so plain shared
-    // loads and stores ordered by __syncwarp suffice)
+    // counts first: each warp counts its keys' digits in its own histogram
     uint32_t* wh = warp_hist + warp * 256;
     const uint32_t lt_mask = (1u << lane) - 1;
 #pragma unroll
-    for (int i = 0; i < ITEMS; i++) {
-        const bool valid = full || (w0 + 32 * i < tile_n);
-        const uint32_t dg = valid ? key_digit<NW>(k[i], shift) : 256u;
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg);
-        const int leader = __ffs(peers) - 1;
-        const uint32_t old = valid ? wh[dg] : 0u;
-        __syncwarp();
-        if (lane == leader && valid) wh[dg] = old + (uint32_t)__popc(peers);
-        __syncwarp();
-        rd[i] = ((old + __popc(peers & lt_mask)) << 8) | (dg & 0xFFu);
-    }
+    for (int i = 0; i < ITEMS; i++)
+        if (full || (w0 + 32 * i < tile_n)) atomicAdd(&wh[key_digit<NW>(k[i], shift)], 1u);
     __syncthreads();
     // per digit: exclusive prefix over warps, tile total
     const int d = tid;  // kSortThreads == 256
@@ -169,9 +156,9 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
         warp_hist[w * 256 + d] = cnt;
         cnt += c;
     }
-    // publish this tile's count early so later tiles can proceed (a test
-    // hook, withhold_first, keeps tile 0 from publishing: the next tiles'
-    // bounded waits then run out and report it)
+    // publish this tile's count before ranking, so later tiles can proceed (a
+    // test hook, withhold_first, keeps tile 0 from publishing: the next
+    // tiles' bounded waits then run out and report it)
     uint32_t* st = status + (uint64_t)tile * 256 + d;
     if (!(withhold_first && tile == 0)) st_relaxed_u32(st, (tile == 0 ? kFlagInc : kFlagAgg) | cnt);
     // block exclusive scan of the tile counts -> start of digit d in the tile
@@ -190,19 +177,29 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
         for (int w = 0; w < kSortWarps; w++) wpre += w < warp ? misc[w] : 0u;
         start = wpre + x - cnt;
     }
-    // staging offset of digit d for each warp
+    // each warp's first staging slot for digit d
 #pragma unroll
     for (int w = 0; w < kSortWarps; w++) warp_hist[w * 256 + d] += start;
     __syncthreads();
-    // stage in tile digit order first: it needs no global prefix, and by the
-    // time it is done the earlier tiles have published more of theirs
+    // rank and stage in tile digit order, stable by item then lane: the
+    // lanes holding one digit in one item find each other (match), the
+    // lowest of them takes their slots from the warp's counter in one
+    // atomic add and hands the first slot on; each lane adds the number of
+    // its lower peers.  Staging needs no global prefix, and by the time it
+    // is done the earlier tiles have published more of theirs.
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
-        if (full || (w0 + 32 * i < tile_n)) {
-            const uint32_t pos = wh[rd[i] & 0xFFu] + (rd[i] >> 8);
+        const bool valid = full || (w0 + 32 * i < tile_n);
+        const uint32_t dg = valid ? key_digit<NW>(k[i], shift) : 256u;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg);
+        const int leader = __ffs(peers) - 1;
+        uint32_t slot = 0;
+        if (lane == leader && valid) slot = atomicAdd(&wh[dg], (uint32_t)__popc(peers));
+        slot = __shfl_sync(0xFFFFFFFFu, slot, leader) + (uint32_t)__popc(peers & lt_mask);
+        if (valid) {
 #pragma unroll
-            for (int w = 0; w < NW; w++) stage[w * TILE + pos] = k[i].w[w];
-            if constexpr (HV) vstage[pos] = v[i];
+            for (int w = 0; w < NW; w++) stage[w * TILE + slot] = k[i].w[w];
+            if constexpr (HV) vstage[slot] = v[i];
         }
     }
     // look back over earlier tiles for this digit
