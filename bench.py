@@ -76,7 +76,7 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="metagenome",
                    choices=sorted(WORKLOADS) + ["multik", "served", "batched"])
-    p.add_argument("--e2e-steps", type=int, default=4)
+    p.add_argument("--e2e-steps", type=int, default=8)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the bounded served and batched runs the default metagenome line carries")
@@ -961,8 +961,10 @@ def main():
         torch.cuda.synchronize()
         barrier()
         e0 = time.perf_counter()
+        marks = []
         upload(0)
         for i in range(args.e2e_steps):
+            marks.append(time.perf_counter())
             if i + 1 < args.e2e_steps:
                 upload(i + 1)
             stream.wait_event(up_done[i % 2])
@@ -974,6 +976,7 @@ def main():
             download(g)
             del g, mercy, solid, reads
         torch.cuda.synchronize()
+        marks.append(time.perf_counter())
         e_s = time.perf_counter() - e0
         e_tot = job_totals(dist, "cuda", info["n_kmers"], info["m"], 0.0, e_s)
         e_s = e_tot["e2e_s"]
@@ -986,6 +989,7 @@ def main():
                       "step's compute, the first one not), pack + count + mercy + build through the C ABI, "
                       "the SdBG arrays back to pinned host memory; upload/download/host-wait figures from "
                       "one further step through the library's host-input path, timed part by part",
+               "each_step_ms": [round(1e3 * (b - a), 2) for a, b in zip(marks, marks[1:])],
                "serial_step": serial}
     # roofline of the dominant kernel (radix scatter pass)
     peak, peak_kind = _peak_hbm()

@@ -26,7 +26,7 @@ struct SortItems<2> {
 };
 template <>
 struct SortItems<4> {
-    static constexpr int v = 6;
+    static constexpr int v = 8;
 };
 
 template <int NW, int ITEMS = SortItems<NW>::v>
