@@ -86,6 +86,9 @@ std::vector<Plan> candidate_plans(int nw, int auto_buckets) {
         c.push_back({0, 0, 1, 0, -1});
         for (int sb : {0, 8, -8}) c.push_back({1, 0, 0, sb, -1});
     } else {
+        // wider keys: the unit route with its unit bits as planned and one
+        // fewer or more, the spread route with its pass bits a digit apart
+        for (int ubd : {0, -1, 1}) c.push_back({0, 0, ubd, 0, -1});
         for (int sb : {0, 8, -8}) c.push_back({1, 0, 0, sb, -1});
     }
     if (auto_buckets > 0 && auto_buckets < 6) {

@@ -680,9 +680,8 @@ int count_bucket_bits(mh_ctx* ctx, uint64_t n, int nw) {
 }
 
 // The unit counting (8-bit passes over the top bits, units sorted and
-// counted by a warp each) for 1-word keys, unless the context's plan or
-// MH_COUNT_PATH=spread selects the spread sort with the fix-up and the run
-// pass.
+// counted by a warp each), unless the context's plan or MH_COUNT_PATH=spread
+// selects the spread sort with the fix-up and the run pass.
 static bool use_unit_count(const mh_ctx* ctx) {
     static const bool v = [] {
         const char* e = std::getenv("MH_COUNT_PATH");
@@ -711,21 +710,25 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
     out->n_kmers = 2 * n;
     out->spectrum_mixed = kMixed;
     const int bb = count_bucket_bits(ctx, n, NW);
-    const GroupPlan gp = group_plan(ctx, n, 0);
-    if (bb == 0 && NW == 1 && use_unit_count(ctx) && gp.passes >= 0) {
-        // 1-word keys: 8-bit passes over the top bits, then the units sorted
-        // and counted by a warp each (mh_group.cu)
-        Buf<uint64_t> keys(ctx, n ? n : 1), alt(ctx, n ? n : 1);
+    const GroupPlan gp = group_plan(ctx, n, 0, NW);
+    if (bb == 0 && use_unit_count(ctx) && gp.passes >= 0) {
+        // 8-bit passes over the top bits, then the units sorted and counted
+        // by a warp each (mh_group.cu); the extraction counts the passes'
+        // digits for 1-word keys
+        Buf<uint64_t> keys(ctx, (n ? n : 1) * NW), alt(ctx, (n ? n : 1) * NW);
         const int G = 8 * gp.passes;
-        Buf<uint32_t> hist(ctx, gp.passes ? (size_t)gp.passes * 256 : 1);
-        if (gp.passes) hist.zero();
+        const bool fuse = NW == 1 && gp.passes > 0;
+        Buf<uint32_t> hist(ctx, fuse ? (size_t)gp.passes * 256 : 1);
+        if (fuse) hist.zero();
         if (n)
-            MH_LAUNCH_B(ctx, "extract_canonical", reads->n_packed / 4 + n * 8, grid_for(ctx, F * 32, 256, 8), 256,
-                        gp.passes ? sizeof(uint32_t) * gp.passes * 256 : 0, (extract_canonical_kernel<NW, kMixed>),
-                        reads->packed, reads->frag_offs, woff.p, F, k, keys.p, gp.passes ? hist.p : nullptr, 64 - G,
+            MH_LAUNCH_B(ctx, "extract_canonical", reads->n_packed / 4 + n * 8 * NW, grid_for(ctx, F * 32, 256, 8),
+                        256, fuse ? sizeof(uint32_t) * gp.passes * 256 : 0, (extract_canonical_kernel<NW, kMixed>),
+                        reads->packed, reads->frag_offs, woff.p, F, k, keys.p, fuse ? hist.p : nullptr, 64 - G,
                         gp.passes, 8);
         woff.reset();
-        const bool in_alt = G ? radix_sort<1>(ctx, keys.p, alt.p, nullptr, nullptr, n, 64 - G, 64, hist.p) : false;
+        const bool in_alt =
+            G ? radix_sort<NW>(ctx, keys.p, alt.p, nullptr, nullptr, n, 64 * NW - G, 64 * NW, fuse ? hist.p : nullptr)
+              : false;
         hist.reset();
         Buf<uint64_t>& sorted = in_alt ? alt : keys;
         Buf<uint64_t>& other = in_alt ? keys : alt;
@@ -733,7 +736,7 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
         Buf<uint32_t> sc;
         uint64_t S = 0, runs = 0, palins = 0;
         RunList list;
-        group_count(ctx, sorted, other, n, k, d, 0, gp, sk, sc, &S, &runs, &palins, &list);
+        group_count<NW>(ctx, sorted, other, n, k, d, 0, gp, sk, sc, &S, &runs, &palins, &list);
         sync_and_check(ctx);
         out->n = S;
         out->n_distinct = 2 * runs - palins;
@@ -825,14 +828,14 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
         Buf<uint32_t> sc;
         uint64_t S = 0, runs = 0, palins = 0;
         RunList list;
-        const GroupPlan bp = group_plan(ctx, m, bb);
-        if (NW == 1 && use_unit_count(ctx) && bp.passes >= 0) {
-            const bool in_alt = bp.passes ? radix_sort<1>(ctx, keys.p, alt.p, nullptr, nullptr, m,
-                                                          64 - bb - 8 * bp.passes, 64 - bb)
+        const GroupPlan bp = group_plan(ctx, m, bb, NW);
+        if (use_unit_count(ctx) && bp.passes >= 0) {
+            const bool in_alt = bp.passes ? radix_sort<NW>(ctx, keys.p, alt.p, nullptr, nullptr, m,
+                                                           64 * NW - bb - 8 * bp.passes, 64 * NW - bb)
                                           : false;
             Buf<uint64_t>& sorted = in_alt ? alt : keys;
             Buf<uint64_t>& other = in_alt ? keys : alt;
-            group_count(ctx, sorted, other, m, k, d, bb, bp, sk, sc, &S, &runs, &palins, &list);
+            group_count<NW>(ctx, sorted, other, m, k, d, bb, bp, sk, sc, &S, &runs, &palins, &list);
         } else {
             const bool in_alt = radix_sort_spread<NW>(ctx, keys.p, alt.p, m, bb);
             Buf<uint64_t>& sorted = in_alt ? alt : keys;

@@ -676,22 +676,25 @@ struct RunList {
 // 0 (all in memory) or bits of 2^bits buckets (mh_count.cu).
 int count_bucket_bits(mh_ctx* ctx, uint64_t n, int nw);
 
-// How the unit counting splits n 1-word keys whose top `skip` bits are
-// equal: units of the next unit_bits bits (about 100-160 keys each), sorted
-// into place by `passes` 8-bit LSD passes over the next 8 * passes bits.
-// passes < 0: the keys are too narrow for it (the spread path is used).
+// How the unit counting splits n keys of nw words whose top `skip` bits
+// are equal: units of the next unit_bits bits of the top word (about
+// 160 / 96 / 56 keys each for 1 / 2 / 4 words), sorted into place by
+// `passes` 8-bit LSD passes over the next 8 * passes bits.  passes < 0: the
+// keys are too narrow for it (the spread path is used).
 struct GroupPlan {
     int unit_bits = 0;
     int passes = 0;
 };
-GroupPlan group_plan(mh_ctx* ctx, uint64_t n, int skip);
+GroupPlan group_plan(mh_ctx* ctx, uint64_t n, int skip, int nw);
 
-// Unit counting of mixed canonical 1-word keys (defined in mh_group.cu):
-// `sorted` holds n keys sorted by their top skip + 8 * plan.passes bits,
-// `other` n free words.  Each unit is sorted on chip and run-length counted:
-// out_keys / out_cnt get the kept (k+1)-mers of both strands (count >= d,
-// ascending), list the spectrum (every run's mixed key and length,
-// ascending).  Both input buffers are consumed (freed).
+// Unit counting of mixed canonical keys of NW words (defined in
+// mh_group.cu): `sorted` holds n keys sorted by the top skip + 8 *
+// plan.passes bits of their top word, `other` n free keys.  Each unit is
+// sorted on chip and run-length counted: out_keys / out_cnt get the kept
+// (k+1)-mers of both strands (count >= d, ascending), list the spectrum
+// (every run's mixed key and length, ascending).  Both input buffers are
+// consumed (freed).
+template <int NW>
 void group_count(mh_ctx* ctx, Buf<uint64_t>& sorted, Buf<uint64_t>& other, uint64_t n, int k, int d, int skip,
                  const GroupPlan& plan, Buf<uint64_t>& out_keys, Buf<uint32_t>& out_cnt, uint64_t* n_out,
                  uint64_t* n_runs, uint64_t* n_palin_runs, RunList* list);
