@@ -285,19 +285,20 @@ typedef struct {
 int mh_run_batch(mh_ctx* ctx, const mh_read_set* sets, int n_sets, int k, int d, int workers, int flags,
                  mh_set_result* out);
 
-/* The scatter-pass tile shape the context uses for 1-word keys: 0 = 12 keys
- * a thread at 4 CTAs per SM (the default), 1 = 14 at 3, 2 = 12 at 3; -1
+/* The scatter-pass tile shape the context uses for 1-word keys: 0 = 16 keys
+ * a thread at 3 CTAs per SM (the default), 1 = 12 at 4, 2 = 14 at 3; -1
  * before any autotuning (the default applies). */
 int mh_sort_shape(const mh_ctx* ctx);
 
 /* How the context counts (Sec. 2, third paragraph: the sort and count of
  * every (k+1)-mer).  Every plan gives the same results; only the route and
  * its speed change.  -1 / 0 fields mean the library's default.
- *   path              0: unit counting (1-word keys: 8-bit passes over the
- *                     top bits of the mixed keys, then each unit of about 160
- *                     keys sorted and counted by one warp); 1: the spread
- *                     sort (passes over the top ceil(log2 n) bits, a fix-up of
- *                     keys sharing them, a run pass); wider keys always take 1
+ *   path              0: unit counting (8-bit passes over the top bits of
+ *                     the mixed keys, then each unit of about 160 / 96 / 56
+ *                     keys (1 / 2 / 4 key words) sorted and counted by one
+ *                     warp); 1: the spread sort (passes over the top
+ *                     ceil(log2 n) bits, a fix-up of keys sharing them, a run
+ *                     pass)
  *   sort_shape        the scatter tile shape (see mh_sort_shape)
  *   unit_bits_delta   added to the unit bits of path 0 (-2..2)
  *   spread_bits_delta added to the bits path 1 sorts by passes (-8, 0, 8)
