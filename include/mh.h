@@ -285,6 +285,73 @@ typedef struct {
 int mh_run_batch(mh_ctx* ctx, const mh_read_set* sets, int n_sets, int k, int d, int workers, int flags,
                  mh_set_result* out);
 
+/* Peak device bytes the library plans for one read set through the whole
+ * path at this k (counting dominates: about 48 bytes per window and key
+ * word, plus the packed reads, 512 MB of upload staging for host input and
+ * 64 MB); what mh_run_batch and the server admit jobs by.  0 for NULL or k
+ * outside 2..127. */
+uint64_t mh_job_bytes(const mh_read_set* set, int k);
+
+/* ------------------------------------------------------------ serving */
+
+/* A request server (Sec. 2's whole path per request): jobs (one read set,
+ * k, d) are submitted at any time and taken first in, first out by `slots`
+ * worker threads, each driving a worker context of its own (its own stream
+ * and stream-ordered pool on ctx's device, created with the server).  A job
+ * is admitted when a slot is free and its mh_job_bytes estimate fits
+ * `hbm_budget` next to the jobs running and the results still held, or
+ * when nothing is held (a job larger than the budget runs alone).  A job's
+ * result (solid and mercy tables, SdBG, by the MH_BATCH_* flags) stays on
+ * the device, counted against the budget, until mh_server_release; with
+ * MH_SERVE_AUTO_RELEASE it is freed when the job ends.  MH_SERVE_DRY_RUN
+ * runs no device work (ctx may be NULL): a job takes n_reads microseconds
+ * on the host and gives no outputs, so the scheduling can be tested without
+ * a GPU.  The read set's memory must stay valid until the job has ended. */
+typedef struct mh_server mh_server;
+
+/* A job's record.  Times in seconds on the server's steady clock. */
+typedef struct {
+    double submit_s;
+    double start_s;    /* -1 until admitted */
+    double end_s;      /* -1 until ended */
+    int slot;          /* worker that ran it, -1 until admitted */
+    int status;        /* MH_OK, or the error of its first failing step */
+    uint64_t est_bytes;
+} mh_job_info;
+
+#define MH_SERVE_AUTO_RELEASE 8
+#define MH_SERVE_DRY_RUN 16
+
+/* Errors: MH_EINVAL (NULL out, slots outside 1..64, no ctx without
+ * MH_SERVE_DRY_RUN), MH_ENOMEM / MH_EDEVICE (a worker context failed). */
+int mh_server_create(mh_ctx* ctx, int slots, uint64_t hbm_budget, int flags, mh_server** out);
+/* Queues a job; *job gets its id.  MH_EINVAL for NULL arguments, k outside
+ * 2..127 or d < 1, or after mh_server_destroy has begun. */
+int mh_server_submit(mh_server* s, const mh_read_set* set, int k, int d, uint64_t* job);
+/* Waits up to timeout_s seconds (< 0: without limit) for the job to end.
+ * MH_OK once it has ended: out (if not NULL) gets its handles, owned by the
+ * server (NULL when released, failed or skipped), info (if not NULL) its
+ * record, whose status is the job's own result.  MH_ETIMEOUT if it has not
+ * ended in time; MH_EINVAL for an unknown or released id. */
+int mh_server_wait(mh_server* s, uint64_t job, double timeout_s, mh_set_result* out, mh_job_info* info);
+/* Frees an ended job's result, returns its bytes to the budget and drops
+ * its record.  MH_EINVAL for an unknown id or a job still queued or running. */
+int mh_server_release(mh_server* s, uint64_t job);
+/* Bytes held now (running jobs and unreleased results, by estimate), the
+ * most ever held, jobs queued and running.  Any pointer may be NULL. */
+int mh_server_stats(mh_server* s, uint64_t* held_bytes, uint64_t* max_held_bytes, uint64_t* queued,
+                    uint64_t* running);
+/* Starts the most-held figure of mh_server_stats again from what is held
+ * now (to measure one stream of jobs on a server kept warm). */
+int mh_server_reset_max(mh_server* s);
+/* Worker context `slot` (its kernel statistics, mh_trim); NULL for a dry
+ * run or a slot out of range.  Owned by the server. */
+mh_ctx* mh_server_context(mh_server* s, int slot);
+/* Lets every queued and running job end (the results of ended jobs are
+ * freed first, so that queued jobs find room), frees all results, the
+ * worker contexts and the server. */
+int mh_server_destroy(mh_server* s);
+
 /* The scatter-pass tile shape the context uses for 1-word keys: 0 = 16 keys
  * a thread at 3 CTAs per SM (the default), 1 = 12 at 4, 2 = 14 at 3; -1
  * before any autotuning (the default applies). */

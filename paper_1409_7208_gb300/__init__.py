@@ -36,10 +36,12 @@ SYMBOLS = (
     "mh_memory", "mh_profile_count", "mh_profile_get", "mh_profile_reset", "mh_set_profile",
     "mh_sort_keys_noalloc", "mh_walk_contigs", "mh_contigs_view_get", "mh_free_contigs",
     "mh_pack_reads_contigs", "mh_trim", "mh_run_batch", "mh_sort_shape", "mh_get_count_plan",
-    "mh_set_count_plan",
+    "mh_set_count_plan", "mh_job_bytes", "mh_server_create", "mh_server_submit", "mh_server_wait",
+    "mh_server_release", "mh_server_stats", "mh_server_reset_max", "mh_server_context", "mh_server_destroy",
 )
 
 MH_BATCH_MERCY, MH_BATCH_BUILD, MH_BATCH_AUTOTUNE = 1, 2, 4
+MH_SERVE_AUTO_RELEASE, MH_SERVE_DRY_RUN = 8, 16
 
 
 class MhError(RuntimeError):
@@ -84,6 +86,11 @@ class ReadSet(ctypes.Structure):
 class SetResult(ctypes.Structure):
     _fields_ = [("solid", ctypes.c_void_p), ("mercy", ctypes.c_void_p), ("sdbg", ctypes.c_void_p),
                 ("status", ctypes.c_int)]
+
+
+class JobInfo(ctypes.Structure):
+    _fields_ = [("submit_s", ctypes.c_double), ("start_s", ctypes.c_double), ("end_s", ctypes.c_double),
+                ("slot", ctypes.c_int), ("status", ctypes.c_int), ("est_bytes", ctypes.c_uint64)]
 
 
 class ContigsView(ctypes.Structure):
@@ -140,6 +147,18 @@ def load_library(path: str = LIB_PATH):
     lib.mh_sort_shape.argtypes = [P]
     lib.mh_get_count_plan.argtypes = [P, ctypes.POINTER(CountPlan)]
     lib.mh_set_count_plan.argtypes = [P, ctypes.POINTER(CountPlan)]
+    lib.mh_job_bytes.argtypes = [ctypes.POINTER(ReadSet), ctypes.c_int]
+    lib.mh_job_bytes.restype = u64
+    lib.mh_server_create.argtypes = [P, ctypes.c_int, u64, ctypes.c_int, PP]
+    lib.mh_server_submit.argtypes = [P, ctypes.POINTER(ReadSet), ctypes.c_int, ctypes.c_int, ctypes.POINTER(u64)]
+    lib.mh_server_wait.argtypes = [P, u64, ctypes.c_double, ctypes.POINTER(SetResult), ctypes.POINTER(JobInfo)]
+    lib.mh_server_release.argtypes = [P, u64]
+    lib.mh_server_stats.argtypes = [P, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64),
+                                    ctypes.POINTER(u64)]
+    lib.mh_server_reset_max.argtypes = [P]
+    lib.mh_server_context.argtypes = [P, ctypes.c_int]
+    lib.mh_server_context.restype = P
+    lib.mh_server_destroy.argtypes = [P]
     _lib = lib
     return lib
 
@@ -283,7 +302,8 @@ class _Handle:
         self._h = h
 
     def free(self):
-        if getattr(self, "_h", None) and self.ctx._h:
+        # a borrowed handle (a server's result) is freed by its owner
+        if getattr(self, "_h", None) and self.ctx._h and not getattr(self, "borrowed", False):
             getattr(self.ctx._lib, self._free_name)(self._h)
         self._h = None
 

@@ -26,25 +26,8 @@
 
 namespace mh {
 void profile_merge(mh_ctx* dst, mh_ctx* src);
-}  // namespace mh
 
-using namespace mh;
-
-namespace {
-
-constexpr int kSortShapes = 3;
-
-// Peak device bytes of one job: counting dominates (keys, sort buffer, run
-// slots and spectrum: about 48 bytes per window and key word), plus the
-// packed reads, the host upload's staging pieces and a fixed margin.
-uint64_t job_bytes(const mh_read_set& s, int k) {
-    const uint64_t nw = (uint64_t)words_for(k);
-    const uint64_t kk = (uint64_t)k * s.n_reads;
-    const uint64_t win = s.n_bases > kk ? s.n_bases - kk : 0;
-    return (64ull << 20) + 48 * nw * win + 2 * s.n_bases + (s.on_device ? 0 : (512ull << 20));
-}
-
-void free_result(mh_set_result& r) {
+void free_set_result(mh_set_result& r) {
     mh_free_sdbg(r.sdbg);
     mh_free_kmers(r.mercy);
     mh_free_kmers(r.solid);
@@ -52,17 +35,38 @@ void free_result(mh_set_result& r) {
     r.mercy = r.solid = nullptr;
 }
 
-int run_job(mh_ctx* w, const mh_read_set& s, int k, int d, int flags, mh_set_result& r) {
+int run_set_job(mh_ctx* w, const mh_read_set& s, int k, int d, int flags, mh_set_result& r) {
     mh_reads* reads = nullptr;
     int rc = mh_pack_reads(w, s.ascii, s.n_bases, s.offs, s.n_reads, s.on_device, &reads);
     if (rc == MH_OK) rc = mh_count_kmers(w, reads, k, d, &r.solid);
     if (rc == MH_OK && (flags & MH_BATCH_MERCY)) rc = mh_mercy_kmers(w, reads, r.solid, &r.mercy);
     if (rc == MH_OK && (flags & MH_BATCH_BUILD)) rc = mh_build_sdbg(w, r.solid, r.mercy, &r.sdbg);
     mh_free_reads(reads);
-    if (rc != MH_OK) free_result(r);
+    if (rc != MH_OK) free_set_result(r);
     r.status = rc;
     return rc;
 }
+}  // namespace mh
+
+// Peak device bytes of one job: counting dominates (keys, sort buffer, run
+// slots and spectrum: about 48 bytes per window and key word), plus the
+// packed reads, the host upload's staging pieces and a fixed margin.
+extern "C" uint64_t mh_job_bytes(const mh_read_set* s, int k) {
+    if (!s || k < 2 || k > 127) return 0;
+    const uint64_t nw = (uint64_t)mh::words_for(k);
+    const uint64_t kk = (uint64_t)k * s->n_reads;
+    const uint64_t win = s->n_bases > kk ? s->n_bases - kk : 0;
+    return (64ull << 20) + 48 * nw * win + 2 * s->n_bases + (s->on_device ? 0 : (512ull << 20));
+}
+
+using namespace mh;
+
+namespace {
+
+constexpr int kSortShapes = 3;
+
+uint64_t job_bytes(const mh_read_set& s, int k) { return mh_job_bytes(&s, k); }
+
 
 using Plan = std::vector<int>;  // path, sort_shape, unit_bits_delta, spread_bits_delta, bucket_bits
 
@@ -239,7 +243,7 @@ int mh_run_batch(mh_ctx* ctx, const mh_read_set* sets, int n_sets, int k, int d,
                     est = job_bytes(sets[j], k);
                     held += est;
                 }
-                run_job(w, sets[j], k, d, flags, out[j]);
+                run_set_job(w, sets[j], k, d, flags, out[j]);
                 {
                     std::lock_guard<std::mutex> lock(mu);
                     held -= est;

@@ -652,6 +652,11 @@ template <int NW>
 void set_differences(mh_ctx* ctx, const uint64_t* X, uint64_t nx, const uint64_t* Y, uint64_t ny, uint64_t* outX,
                      uint64_t* n_outX, uint64_t* outY, uint64_t* n_outY);
 
+// One read set through pack, count and (by flags) mercy and build on
+// context w (mh_batch.cu); a failed set keeps no outputs.
+int run_set_job(mh_ctx* w, const mh_read_set& s, int k, int d, int flags, mh_set_result& r);
+void free_set_result(mh_set_result& r);
+
 template <int NW>
 void walk_contigs(mh_ctx* ctx, const mh_kmers* solid, const mh_kmers* mercy, uint64_t n_walks, uint32_t max_len,
                   uint64_t seed, mh_contigs* out);

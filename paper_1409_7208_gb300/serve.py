@@ -1,57 +1,82 @@
-"""Serving: a request loop over the C ABI with continuous batching.
+"""Serving over the C ABI: a thin wrapper of the library's request server
+(``mh_server_*``).
 
-Jobs (one read set, k, d) arrive at any time.  A fixed number of worker
-slots, each with its own library context and CUDA stream, take jobs from
-one FIFO queue; a job is admitted when a slot is free and its estimated
-device memory fits the HBM budget next to the jobs in flight and the
-results still held on the device.  Jobs that arrive while others run are
-admitted as slots and memory free up, and their work overlaps on the device
-(one stream per slot).  A job's result (solid and mercy tables, SdBG) stays
-resident until the client releases it, and counts against the budget until
-then.  Host logic only: every step of a job runs in libmh's kernels.
+Jobs (one read set, k, d) arrive at any time.  The server's ``slots``
+worker threads, each with a worker context of its own (stream and
+stream-ordered pool), take jobs from one first-in first-out queue; a job is
+admitted when a slot is free and its estimated device memory
+(``mh_job_bytes``) fits the HBM budget next to the jobs running and the
+results still held, or when nothing is held.  Jobs that arrive while others
+run are admitted as slots and memory free up, and their work overlaps on the
+device.  A job's result (solid and mercy tables, SdBG) stays resident until
+the client releases it, and counts against the budget until then.  The
+scheduling and every step of a job run in libmh; this module only marshals
+arguments and converts the server's clock to ``time.perf_counter``.
 """
 from __future__ import annotations
 
-import collections
-import threading
+import ctypes
 import time
 
+import numpy as np
 
-def key_words(k: int) -> int:
-    return 1 if 2 * (k + 1) <= 64 else (2 if 2 * (k + 1) <= 128 else 4)
+from . import (MH_BATCH_BUILD, MH_BATCH_MERCY, MH_ETIMEOUT, MH_OK, MH_SERVE_AUTO_RELEASE, MH_SERVE_DRY_RUN,
+               Context, JobInfo, Kmers, MhError, ReadSet, Sdbg, SetResult, _ptr_of, _strerror, load_library)
 
 
-def estimate_bytes(n_bases: int, n_reads: int, k: int) -> int:
-    """Peak device bytes of one job (measured: about 40 bytes per window and
-    key word for counting, which dominates), plus a fixed 64 MB."""
-    windows = max(0, n_bases - n_reads * k)
-    return (64 << 20) + 48 * key_words(k) * windows + 2 * n_bases
+def _read_set(ascii, offs):
+    """(ReadSet, kept arrays) for host numpy arrays or torch tensors."""
+    if isinstance(ascii, np.ndarray):
+        ascii = np.ascontiguousarray(ascii, dtype=np.uint8)
+        offs = np.ascontiguousarray(offs, dtype=np.uint64)
+    pa, da = _ptr_of(ascii)
+    po, do = _ptr_of(offs)
+    if da != do:
+        raise ValueError("ascii and offs must both be on the host or both on the device")
+    n_bases = int(ascii.shape[0])
+    return ReadSet(pa if n_bases else None, n_bases, po, int(offs.shape[0]) - 1, da), (ascii, offs)
+
+
+def estimate_bytes(ascii, offs, k: int) -> int:
+    """The library's admission estimate for one job (``mh_job_bytes``)."""
+    rs, _ = _read_set(ascii, offs)
+    return int(load_library().mh_job_bytes(ctypes.byref(rs), int(k)))
 
 
 class Job:
-    """A count + mercy + build request."""
+    """A count + mercy + build request.  Times (``submit_t``, ``start_t``,
+    ``end_t``) are on ``time.perf_counter``'s clock."""
 
     def __init__(self, ascii, offs, k: int, d: int = 2, tag=None):
         self.ascii, self.offs, self.k, self.d, self.tag = ascii, offs, k, d, tag
         self.n_bases = int(len(ascii))
         self.n_reads = int(len(offs)) - 1
-        self.est = estimate_bytes(self.n_bases, self.n_reads, k)
+        self.est = estimate_bytes(ascii, offs, k)
         self.submit_t = self.start_t = self.end_t = None
-        self.result = None
-        self.error = None
         self.slot = None
-        self.done = threading.Event()
+        self.status = None
+        self.result = None
+        self.id = None
         self._server = None
+        self._keep = None
 
     @property
     def latency(self) -> float:
         return self.end_t - self.submit_t
 
+    def finished(self) -> bool:
+        """True once the job has ended (without waiting)."""
+        return self._server is not None and self._server._wait(self, 0.0)
+
     def wait(self, timeout=None) -> "Job":
-        if not self.done.wait(timeout):
+        """Wait for the job to end; raises TimeoutError if it has not ended
+        within ``timeout`` seconds, MhError if it failed."""
+        if self._server is None:
+            raise RuntimeError("job not submitted, or already released")
+        if not self._server._wait(self, -1.0 if timeout is None else float(timeout)):
             raise TimeoutError("job not finished")
-        if self.error is not None:
-            raise self.error
+        if self.status != MH_OK:
+            raise MhError(self.status, "job %r failed: %s" % (self.tag, _strerror(self.status)))
         return self
 
     def release(self):
@@ -60,112 +85,113 @@ class Job:
             self._server._release(self)
 
 
-class Server:
-    """``slots`` workers under an HBM budget.  ``runner(job, slot)`` runs a
-    job and returns its result (a dict of resident handles); the default
-    runs the library on GPU ``device``.  ``auto_release`` frees each result
-    as soon as its job completes."""
+class _WorkerContext(Context):
+    """A server's worker context, owned by the server: its kernel statistics
+    and the device its results live on."""
 
-    def __init__(self, slots: int = 4, hbm_budget: int = 150 << 30, runner=None, device: int = 0,
-                 auto_release: bool = False):
+    def __init__(self, lib, h, device: int):
+        import torch
+        self._lib, self._h = lib, h
+        self.device = torch.device("cuda", device)
+
+    def close(self):
+        self._h = None
+
+
+class Server:
+    """``slots`` workers under an HBM budget on GPU ``device``.
+    ``auto_release`` frees each result as soon as its job ends.  ``dry_run``
+    runs no device work (a job takes ``n_reads`` microseconds on the host):
+    the scheduling alone, without a GPU."""
+
+    def __init__(self, slots: int = 4, hbm_budget: int = 150 << 30, device: int = 0, auto_release: bool = False,
+                 dry_run: bool = False):
+        lib = load_library()
+        self._lib = lib
         self.slots = slots
         self.budget = hbm_budget
-        self.auto_release = auto_release
-        self.runner = runner if runner is not None else DeviceRunner(device, slots)
-        self._q = collections.deque()
-        self._cv = threading.Condition()
-        self._held = 0          # bytes of admitted, unreleased jobs
-        self.max_held = 0
-        self._stop = False
-        self._threads = [threading.Thread(target=self._worker, args=(i,), daemon=True) for i in range(slots)]
-        for t in self._threads:
-            t.start()
+        self.dry_run = dry_run
+        self.ctx = None if dry_run else Context(device=device, torch_allocator=False)
+        flags = MH_BATCH_MERCY | MH_BATCH_BUILD | (MH_SERVE_AUTO_RELEASE if auto_release else 0) | \
+            (MH_SERVE_DRY_RUN if dry_run else 0)
+        h = ctypes.c_void_p()
+        self._t0 = time.perf_counter()  # the server's clock starts inside the call
+        rc = lib.mh_server_create(self.ctx.handle if self.ctx else None, int(slots), int(hbm_budget), flags,
+                                  ctypes.byref(h))
+        if rc != MH_OK:
+            raise MhError(rc, "mh_server_create failed")
+        self._h = h
+        self.contexts = [] if dry_run else [
+            _WorkerContext(lib, lib.mh_server_context(h, i), device) for i in range(slots)]
 
     def submit(self, job: Job) -> Job:
-        job.submit_t = time.perf_counter()
+        rs, job._keep = _read_set(job.ascii, job.offs)
+        jid = ctypes.c_uint64()
+        rc = self._lib.mh_server_submit(self._h, ctypes.byref(rs), int(job.k), int(job.d), ctypes.byref(jid))
+        if rc != MH_OK:
+            raise MhError(rc, "mh_server_submit failed")
+        job.id = jid.value
         job._server = self
-        with self._cv:
-            self._q.append(job)
-            self._cv.notify_all()
         return job
 
-    def _fits(self, job: Job) -> bool:
-        # a job larger than the whole budget runs when nothing else is held
-        return self._held + job.est <= self.budget or self._held == 0
-
-    def _worker(self, slot: int):
-        while True:
-            with self._cv:
-                while not self._stop and not (self._q and self._fits(self._q[0])):
-                    self._cv.wait()
-                if self._stop and not self._q:
-                    return
-                job = self._q.popleft()
-                self._held += job.est
-                self.max_held = max(self.max_held, self._held)
-                self._cv.notify_all()
-            job.slot = slot
-            job.start_t = time.perf_counter()
-            try:
-                job.result = self.runner(job, slot)
-            except Exception as e:  # the job fails; the server keeps serving
-                job.error = e
-            job.end_t = time.perf_counter()
-            if self.auto_release or job.error is not None:
-                self._release(job)
-            job.done.set()
+    def _wait(self, job: Job, timeout: float) -> bool:
+        res, info = SetResult(), JobInfo()
+        rc = self._lib.mh_server_wait(self._h, job.id, timeout, ctypes.byref(res), ctypes.byref(info))
+        if rc == MH_ETIMEOUT:
+            return False
+        if rc != MH_OK:
+            raise MhError(rc, "mh_server_wait failed")
+        job.submit_t = self._t0 + info.submit_s
+        job.start_t = self._t0 + info.start_s
+        job.end_t = self._t0 + info.end_s
+        job.slot = info.slot
+        job.status = info.status
+        if job.result is None and res.solid:
+            wc = self.contexts[info.slot]
+            job.result = {"solid": Kmers(wc, res.solid), "mercy": Kmers(wc, res.mercy) if res.mercy else None,
+                          "sdbg": Sdbg(wc, res.sdbg) if res.sdbg else None}
+            for v in job.result.values():
+                if v is not None:
+                    v.borrowed = True
+        return True
 
     def _release(self, job: Job):
-        with self._cv:
-            if job._server is None:
-                return
-            job._server = None
-            if isinstance(job.result, dict):
-                for h in job.result.values():
-                    if hasattr(h, "free"):
-                        h.free()
-            job.result = None
-            self._held -= job.est
-            self._cv.notify_all()
+        if job._server is not self:
+            return
+        rc = self._lib.mh_server_release(self._h, job.id)
+        if rc != MH_OK:
+            raise MhError(rc, "mh_server_release: the job has not ended")
+        if isinstance(job.result, dict):
+            for v in job.result.values():
+                if v is not None:
+                    v._h = None
+        job.result = None
+        job._server = None
+        job._keep = None
+
+    def stats(self) -> dict:
+        a, b, c, d = (ctypes.c_uint64() for _ in range(4))
+        self._lib.mh_server_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d))
+        return {"held": a.value, "max_held": b.value, "queued": c.value, "running": d.value}
+
+    @property
+    def max_held(self) -> int:
+        return self.stats()["max_held"]
+
+    def reset_max(self):
+        self._lib.mh_server_reset_max(self._h)
 
     def close(self):
-        with self._cv:
-            self._stop = True
-            self._cv.notify_all()
-        for t in self._threads:
-            t.join()
+        if getattr(self, "_h", None):
+            self._lib.mh_server_destroy(self._h)
+            self._h = None
+            for c in self.contexts:
+                c.close()
+            if self.ctx is not None:
+                self.ctx.close()
 
-
-class DeviceRunner:
-    """One library context and one CUDA stream per slot.  The contexts use
-    the library's own stream-ordered pools (no Python in the allocation
-    path, so the slots' host threads do not contend for the interpreter);
-    a slot trims its pool after a job above ``trim_bytes``."""
-
-    def __init__(self, device: int, slots: int, trim_bytes: int = 8 << 30):
-        import torch
-
-        from . import Context
-        self.trim_bytes = trim_bytes
-        self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
-        self.ctxs = [Context(device=device, stream=s, torch_allocator=False) for s in self.streams]
-
-    def __call__(self, job: Job, slot: int) -> dict:
-        import torch
-
-        from . import mh_build_sdbg, mh_count_kmers, mh_mercy_kmers, mh_pack_reads
-        ctx, s = self.ctxs[slot], self.streams[slot]
-        with torch.cuda.stream(s):
-            reads = mh_pack_reads(ctx, job.ascii, job.offs)
-            solid = mh_count_kmers(ctx, reads, job.k, job.d)
-            mercy = mh_mercy_kmers(ctx, reads, solid)
-            sdbg = mh_build_sdbg(ctx, solid, mercy)
-            reads.free()
-        s.synchronize()
-        if job.est > self.trim_bytes:
-            ctx.trim()
-        return {"solid": solid, "mercy": mercy, "sdbg": sdbg}
-
-    def close(self):
-        for c in self.ctxs:
-            c.close()
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

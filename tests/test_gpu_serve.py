@@ -1,6 +1,8 @@
-"""Serving on the GPU: every job's result is the same alone and in the mix
-(jobs of different sizes and k admitted while others run, on four streams),
-bit for bit; and a mixed job agrees with the oracle."""
+"""Serving on the GPU through the library's request server: every job's
+result is the same alone and in the mix (jobs of different sizes and k
+admitted while others run, on four streams), bit for bit, and a mixed job
+agrees with the oracle; a failing job is reported while the others finish;
+the admission estimate covers each job's measured peak."""
 import time
 
 import numpy as np
@@ -60,3 +62,51 @@ def test_results_alone_equal_results_in_the_mix():
     for j in jobs:
         j.release()
     srv.close()
+
+
+def test_failed_job_is_reported_and_the_others_run():
+    """A job whose read offsets run backwards fails in the packing step with
+    its error; the jobs around it finish and match the oracle."""
+    from paper_1409_7208_gb300 import MhError, serve
+    good = _jobs()[:3]
+    ascii, offs = synth.uniform_genome_reads(77, 5000, 200, 100, 0.01)
+    bad_offs = offs.copy()
+    bad_offs[5], bad_offs[6] = bad_offs[6], bad_offs[5]
+    bad = serve.Job(ascii, bad_offs, 31, 2, tag="bad")
+    srv = serve.Server(slots=2, hbm_budget=1 << 40)
+    for j in (good[0], bad, good[1], good[2]):
+        srv.submit(j)
+    with pytest.raises(MhError):
+        bad.wait(120)
+    for j in good:
+        j.wait(120)
+    w = oracle.count(good[2].ascii, good[2].offs, good[2].k, 2, mercy=True)
+    got = _fetch(good[2])
+    assert np.array_equal(got["sk"], w["solid_keys"]) and np.array_equal(got["mk"], w["mercy_keys"])
+    for j in good + [bad]:
+        j.release()
+    assert srv.stats()["held"] == 0
+    srv.close()
+
+
+def test_admission_estimate_covers_the_measured_peak():
+    """mh_job_bytes, the estimate jobs are admitted by, is at least the
+    device memory a job really holds at its peak (the library's own pool,
+    host input, whole path), for every key width."""
+    import paper_1409_7208_gb300 as mh
+    from paper_1409_7208_gb300 import serve
+    # sizes where the per-window term of the estimate outweighs its fixed part
+    for seed, (n_reads, L, k) in enumerate([(200000, 150, 21), (200000, 150, 31), (150000, 150, 47),
+                                            (80000, 150, 99), (300000, 100, 27)]):
+        ascii, offs = synth.uniform_genome_reads(300 + seed, 2000000, n_reads, L, 0.01)
+        ctx = mh.Context(device=0, torch_allocator=False)
+        reads = mh.mh_pack_reads(ctx, ascii, offs)
+        solid = mh.mh_count_kmers(ctx, reads, k, 2)
+        mercy = mh.mh_mercy_kmers(ctx, reads, solid)
+        g = mh.mh_build_sdbg(ctx, solid, mercy)
+        peak = ctx.memory()[1]
+        est = serve.estimate_bytes(ascii, offs, k)
+        assert 0 < peak <= est, (k, peak, est)
+        for h in (g, mercy, solid, reads):
+            h.free()
+        ctx.close()
