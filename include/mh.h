@@ -193,6 +193,19 @@ typedef struct {
 int mh_sdbg_view_get(const mh_sdbg* g, mh_sdbg_view* v);
 void mh_free_sdbg(mh_sdbg* g);
 
+/* The graph in one flat little-endian file ("MHSDBG01", a header with k, nw,
+ * m, t, u, the node count and F, then W, last, valid, dummy, aux and mult
+ * when present, then an FNV-1a hash of every byte before it), so that it
+ * outlives the process.  mh_sdbg_save waits for the graph's stream and
+ * copies through host memory.  mh_sdbg_load checks the magic, the header
+ * and the sizes against the file's length before it allocates, and the hash
+ * after reading; the graph it returns is owned by the caller (mh_free_sdbg)
+ * and lives on ctx's device.  Errors: MH_EINVAL (NULL, a file that cannot
+ * be opened, written or read, or that is not a whole, undamaged graph file;
+ * nothing is returned then), MH_ENOMEM, MH_EDEVICE. */
+int mh_sdbg_save(const mh_sdbg* g, const char* path);
+int mh_sdbg_load(mh_ctx* ctx, const char* path, mh_sdbg** out);
+
 /* ------------------------------------------- multiple-k iteration */
 
 /* The paper (Sec. 2 fourth paragraph, Sec. 3) builds the graph for a list of

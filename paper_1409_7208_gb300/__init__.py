@@ -38,6 +38,7 @@ SYMBOLS = (
     "mh_pack_reads_contigs", "mh_trim", "mh_run_batch", "mh_sort_shape", "mh_get_count_plan",
     "mh_set_count_plan", "mh_job_bytes", "mh_server_create", "mh_server_submit", "mh_server_wait",
     "mh_server_release", "mh_server_stats", "mh_server_reset_max", "mh_server_context", "mh_server_destroy",
+    "mh_sdbg_save", "mh_sdbg_load",
 )
 
 MH_BATCH_MERCY, MH_BATCH_BUILD, MH_BATCH_AUTOTUNE = 1, 2, 4
@@ -159,6 +160,8 @@ def load_library(path: str = LIB_PATH):
     lib.mh_server_context.argtypes = [P, ctypes.c_int]
     lib.mh_server_context.restype = P
     lib.mh_server_destroy.argtypes = [P]
+    lib.mh_sdbg_save.argtypes = [P, ctypes.c_char_p]
+    lib.mh_sdbg_load.argtypes = [P, ctypes.c_char_p, PP]
     _lib = lib
     return lib
 
@@ -480,6 +483,19 @@ def mh_build_sdbg(ctx: Context, solid: Kmers, mercy: Kmers | None = None) -> Sdb
     h = ctypes.c_void_p()
     ctx._check(ctx._lib.mh_build_sdbg(ctx._h, solid._h, mercy._h if mercy is not None else None,
                                       ctypes.byref(h)))
+    return Sdbg(ctx, h)
+
+
+
+def mh_sdbg_save(g: Sdbg, path: str):
+    """Write the graph to one flat file (see include/mh.h)."""
+    g.ctx._check(g.ctx._lib.mh_sdbg_save(g._h, os.fsencode(path)))
+
+
+def mh_sdbg_load(ctx: Context, path: str) -> Sdbg:
+    """Read a graph written by :func:`mh_sdbg_save` onto ctx's device."""
+    h = ctypes.c_void_p()
+    ctx._check(ctx._lib.mh_sdbg_load(ctx._h, os.fsencode(path), ctypes.byref(h)))
     return Sdbg(ctx, h)
 
 
