@@ -120,7 +120,7 @@ static void drain_events(mh_ctx* ctx, bool wait) {
     ctx->pending.resize(keep);
 }
 
-Prof::Prof(mh_ctx* c, const char* name, uint64_t algo_bytes) : ctx(c), bytes(algo_bytes) {
+Prof::Prof(mh_ctx* c, const char* name, uint64_t algo_bytes) : range(name), ctx(c), bytes(algo_bytes) {
     if (!ctx->profile) return;
     auto it = ctx->name_id.find(name);
     if (it == ctx->name_id.end()) {
@@ -285,6 +285,7 @@ void mh_destroy(mh_ctx* ctx) {
 
 int mh_pack_reads(mh_ctx* ctx, const uint8_t* ascii, uint64_t n_bases, const uint64_t* offs, uint64_t n_reads,
                   int on_device, mh_reads** out) {
+    NvtxRange nvtx("mh_pack_reads");
     if (!ctx || !out || !offs || (!ascii && n_bases)) return MH_EINVAL;
     *out = nullptr;
     return guarded(ctx, [&] {
@@ -304,6 +305,7 @@ int mh_pack_reads(mh_ctx* ctx, const uint8_t* ascii, uint64_t n_bases, const uin
 
 int mh_pack_reads_contigs(mh_ctx* ctx, const uint8_t* ascii, uint64_t n_bases, const uint64_t* offs,
                           uint64_t n_reads, const mh_contigs* contigs, int copies, mh_reads** out) {
+    NvtxRange nvtx("mh_pack_reads_contigs");
     if (!ctx || !out || !offs || (!ascii && n_bases) || copies < 0) return MH_EINVAL;
     *out = nullptr;
     return guarded(ctx, [&] {
@@ -317,6 +319,7 @@ int mh_pack_reads_contigs(mh_ctx* ctx, const uint8_t* ascii, uint64_t n_bases, c
 
 int mh_walk_contigs(mh_ctx* ctx, const mh_kmers* solid, const mh_kmers* mercy, uint64_t n_walks, uint64_t max_len,
                     uint64_t seed, mh_contigs** out) {
+    NvtxRange nvtx("mh_walk_contigs");
     if (!ctx || !solid || !out) return MH_EINVAL;
     *out = nullptr;
     if ((mercy && mercy->k != solid->k) || max_len < (uint64_t)solid->k + 1 || max_len >= (1ull << 24) ||
@@ -375,6 +378,7 @@ void mh_free_reads(mh_reads* r) {
 }
 
 int mh_count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers** out) {
+    NvtxRange nvtx("mh_count_kmers");
     if (!ctx || !reads || !out || k < 2 || k > 127 || d < 1) {
         if (ctx) ctx->last_error = "mh_count_kmers: need ctx, reads, out, 2 <= k <= 127, d >= 1";
         return MH_EINVAL;
@@ -394,6 +398,7 @@ int mh_count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers** 
 }
 
 int mh_mercy_kmers(mh_ctx* ctx, const mh_reads* reads, const mh_kmers* solid, mh_kmers** out) {
+    NvtxRange nvtx("mh_mercy_kmers");
     if (!ctx || !reads || !solid || !out) return MH_EINVAL;
     *out = nullptr;
     if (!solid->spectrum) {
@@ -435,6 +440,7 @@ void mh_free_kmers(mh_kmers* s) {
 }
 
 int mh_build_sdbg(mh_ctx* ctx, const mh_kmers* solid, const mh_kmers* mercy, mh_sdbg** out) {
+    NvtxRange nvtx("mh_build_sdbg");
     if (!ctx || !solid || !out) return MH_EINVAL;
     *out = nullptr;
     if (mercy && mercy->k != solid->k) {

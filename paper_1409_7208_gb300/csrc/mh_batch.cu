@@ -36,6 +36,7 @@ void free_set_result(mh_set_result& r) {
 }
 
 int run_set_job(mh_ctx* w, const mh_read_set& s, int k, int d, int flags, mh_set_result& r) {
+    NvtxRange nvtx("mh_set_job");
     mh_reads* reads = nullptr;
     int rc = mh_pack_reads(w, s.ascii, s.n_bases, s.offs, s.n_reads, s.on_device, &reads);
     if (rc == MH_OK) rc = mh_count_kmers(w, reads, k, d, &r.solid);
@@ -171,6 +172,7 @@ int mh_set_count_plan(mh_ctx* ctx, const mh_count_plan* p) {
 
 int mh_run_batch(mh_ctx* ctx, const mh_read_set* sets, int n_sets, int k, int d, int workers, int flags,
                  mh_set_result* out) {
+    NvtxRange nvtx("mh_run_batch");
     if (!ctx || n_sets < 0 || (n_sets && (!sets || !out)) || workers < 1 || workers > 64 || k < 2 || k > 127 ||
         d < 1) {
         if (ctx) ctx->last_error = "mh_run_batch: need ctx, sets, out, n_sets >= 0, 1 <= workers <= 64, "

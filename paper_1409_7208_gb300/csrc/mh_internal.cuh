@@ -18,6 +18,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mh.h"
 
 namespace mh {
@@ -175,7 +177,18 @@ struct Buf {
 };
 
 // ------------------------------------------------------ launch profiling
+// An NVTX range (named in a profiler's timeline) for the scope: every public
+// call and every kernel launch opens one.  Without a tool attached the calls
+// return at once.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 struct Prof {
+    NvtxRange range;
     mh_ctx* ctx;
     int id = -1;
     uint64_t bytes = 0;

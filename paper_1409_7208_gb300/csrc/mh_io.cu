@@ -96,6 +96,7 @@ extern "C" {
 
 int mh_sdbg_save(const mh_sdbg* g, const char* path) {
     if (!g || !path || !g->ctx) return MH_EINVAL;
+    NvtxRange nvtx("mh_sdbg_save");
     mh_ctx* ctx = g->ctx;
     try {
         if (cudaSetDevice(ctx->device) != cudaSuccess) throw Error{MH_EDEVICE, "cudaSetDevice failed"};
@@ -136,6 +137,7 @@ int mh_sdbg_save(const mh_sdbg* g, const char* path) {
 
 int mh_sdbg_load(mh_ctx* ctx, const char* path, mh_sdbg** out) {
     if (!ctx || !path || !out) return MH_EINVAL;
+    NvtxRange nvtx("mh_sdbg_load");
     *out = nullptr;
     mh_sdbg* g = nullptr;
     try {
