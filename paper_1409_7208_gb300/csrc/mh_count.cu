@@ -32,8 +32,11 @@ __global__ void frag_windows_kernel(const uint64_t* __restrict__ frag_offs, uint
     }
 }
 
-// Warp per fragment: canonical key of every window, written at woff[f] + i
-// (MIXED: its mix_bij image, 1-word keys).  With `hist` (1-word keys), the
+// Fragments of at most this many windows are extracted by one lane.
+constexpr int kLaneWindows = 48;
+
+// Canonical key of every window of every fragment, window i of fragment f
+// written at woff[f] + i (MIXED: as its mix_key image).  With `hist` (1-word keys), the
 // block also counts the digits the sort's passes will use (n_passes digits of
 // rb bits from bit shift0; in dynamic shared memory, added to hist at the
 // end), so the sort needs no histogram pass of its own.
@@ -55,37 +58,52 @@ __global__ void __launch_bounds__(256) extract_canonical_kernel(const uint32_t* 
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const int K1 = k + 1;
-    // the next fragment's bounds load while this one is extracted
-    uint64_t b = 0, w0 = 0, w1 = 0;
-    if (warp < n_frags) {
-        b = frag_offs[warp];
-        w0 = woff[warp];
-        w1 = woff[warp + 1];
-    }
-    for (uint64_t f = warp; f < n_frags; f += n_warps) {
-        const uint64_t fn = f + n_warps;
-        uint64_t nb = 0, nw0 = 0, nw1 = 0;
-        if (fn < n_frags) {
-            nb = frag_offs[fn];
-            nw0 = woff[fn];
-            nw1 = woff[fn + 1];
+    // the canonical key of window `at` (forward key x, reverse complement r)
+    auto put = [&](uint64_t at, const Key<NW>& x, const Key<NW>& r) {
+        Key<NW> c = key_less<NW>(r, x) ? r : x;
+        if constexpr (MIXED) c = mix_key<NW>(c);
+        store_key<NW>(out, at, c);
+        if constexpr (NW == 1) {
+            if (hist)
+                for (int p = 0; p < n_passes; p++)
+                    atomicAdd(&sh[(p << rb) + ((uint32_t)(c.w[0] >> (shift0 + rb * p)) & dmask)], 1u);
         }
-        const uint64_t nw = w1 - w0;
-        for (uint64_t i = lane; i < nw; i += 32) {
-            Key<NW> x = load_window<NW>(packed, b + i, K1);
+    };
+    // fragments in groups of 32 a warp: a fragment of at most kLaneWindows
+    // windows is taken by one lane, which assembles its first key and its
+    // reverse complement and rolls both on by one symbol a window (short
+    // reads at a large k leave most lanes of a warp per fragment idle);
+    // longer fragments are then taken by the whole warp, a window a lane
+    for (uint64_t g = warp; g * 32 < n_frags; g += n_warps) {
+        const uint64_t f = g * 32 + lane;
+        uint64_t b = 0, w0 = 0, nw = 0;
+        if (f < n_frags) {
+            b = frag_offs[f];
+            w0 = woff[f];
+            nw = woff[f + 1] - w0;
+        }
+        const bool alone = nw <= (uint64_t)kLaneWindows;
+        if (alone && nw) {
+            Key<NW> x = load_window<NW>(packed, b, K1);
             Key<NW> r = key_rc<NW>(x, K1);
-            Key<NW> c = key_less<NW>(r, x) ? r : x;
-            if constexpr (MIXED) c = mix_key<NW>(c);
-            store_key<NW>(out, w0 + i, c);
-            if constexpr (NW == 1) {
-                if (hist)
-                    for (int p = 0; p < n_passes; p++)
-                        atomicAdd(&sh[(p << rb) + ((uint32_t)(c.w[0] >> (shift0 + rb * p)) & dmask)], 1u);
+            for (uint64_t i = 0;;) {
+                put(w0 + i, x, r);
+                if (++i >= nw) break;
+                roll_window<NW>(x, r, packed_sym(packed, b + i + K1 - 1), K1);
             }
         }
-        b = nb;
-        w0 = nw0;
-        w1 = nw1;
+        uint32_t big = __ballot_sync(0xFFFFFFFFu, !alone);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const uint64_t fb = __shfl_sync(0xFFFFFFFFu, b, src);
+            const uint64_t fw0 = __shfl_sync(0xFFFFFFFFu, w0, src);
+            const uint64_t fnw = __shfl_sync(0xFFFFFFFFu, nw, src);
+            for (uint64_t i = lane; i < fnw; i += 32) {
+                const Key<NW> x = load_window<NW>(packed, fb + i, K1);
+                put(fw0 + i, x, key_rc<NW>(x, K1));
+            }
+        }
     }
     if (hist) {
         __syncthreads();

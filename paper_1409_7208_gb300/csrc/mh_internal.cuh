@@ -327,6 +327,31 @@ __device__ __forceinline__ Key<NW> key_or_low(Key<NW> a, uint64_t v) {
     return a;
 }
 
+// The next window of a read from the current one: x (the window, K1
+// symbols, first symbol most significant) shifted up by one symbol with the
+// new symbol s appended and its first symbol dropped; r, its reverse
+// complement, shifted down by one symbol with the complement of s put in
+// front (symbol position K1 - 1).
+template <int NW>
+__device__ __forceinline__ void roll_window(Key<NW>& x, Key<NW>& r, uint32_t s, int K1) {
+#pragma unroll
+    for (int i = NW - 1; i > 0; i--) x.w[i] = (x.w[i] << 2) | (x.w[i - 1] >> 62);
+    x.w[0] = (x.w[0] << 2) | s;
+    x = key_low<NW>(x, 2 * K1);
+#pragma unroll
+    for (int i = 0; i + 1 < NW; i++) r.w[i] = (r.w[i] >> 2) | (r.w[i + 1] << 62);
+    r.w[NW - 1] >>= 2;
+    const int top = 2 * (K1 - 1);
+#pragma unroll
+    for (int i = 0; i < NW; i++)
+        if ((top >> 6) == i) r.w[i] |= (uint64_t)(3u - s) << (top & 63);
+}
+
+// Symbol j of the packed stream (base j at bits 31-2(j%16) of word j/16).
+__device__ __forceinline__ uint32_t packed_sym(const uint32_t* __restrict__ packed, uint64_t j) {
+    return (packed[j >> 4] >> (30 - 2 * (uint32_t)(j & 15))) & 3u;
+}
+
 // Reverse the order of the 2-bit symbols of a 64-bit word.
 __device__ __forceinline__ uint64_t rev2_u64(uint64_t x) {
     uint64_t y = __brevll(x);
