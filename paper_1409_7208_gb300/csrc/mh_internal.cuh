@@ -347,6 +347,15 @@ __device__ __forceinline__ void roll_window(Key<NW>& x, Key<NW>& r, uint32_t s, 
         if ((top >> 6) == i) r.w[i] |= (uint64_t)(3u - s) << (top & 63);
 }
 
+// The forward half of roll_window: the next window from the current one.
+template <int NW>
+__device__ __forceinline__ void roll_forward(Key<NW>& x, uint32_t s, int K1) {
+#pragma unroll
+    for (int i = NW - 1; i > 0; i--) x.w[i] = (x.w[i] << 2) | (x.w[i - 1] >> 62);
+    x.w[0] = (x.w[0] << 2) | s;
+    x = key_low<NW>(x, 2 * K1);
+}
+
 // Symbol j of the packed stream (base j at bits 31-2(j%16) of word j/16).
 __device__ __forceinline__ uint32_t packed_sym(const uint32_t* __restrict__ packed, uint64_t j) {
     return (packed[j >> 4] >> (30 - 2 * (uint32_t)(j & 15))) & 3u;

@@ -339,7 +339,15 @@ __device__ __forceinline__ bool table_has(const Slot<NW>* __restrict__ table, ui
     return false;
 }
 
+// Fragments of at most this many windows are probed by one lane.
+constexpr int kProbeLaneWindows = 48;
+
 // Probe every window; record windows without outdegree as (position, end).
+// Fragments in groups of 32 a warp: a short fragment is probed by one lane,
+// which assembles its first window and rolls it on by one symbol a window
+// (the lanes step together to the group's longest short fragment, so that
+// the hits of a step are counted by one atomic); longer fragments are then
+// probed by the whole warp, a window a lane.
 template <int NW>
 __global__ void __launch_bounds__(256) mercy_probe_kernel(const uint32_t* __restrict__ packed,
                                                           const uint64_t* __restrict__ frag_offs, uint64_t n_frags,
@@ -351,28 +359,59 @@ __global__ void __launch_bounds__(256) mercy_probe_kernel(const uint32_t* __rest
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const int K1 = k + 1;
-    for (uint64_t f = warp; f < n_frags; f += n_warps) {
-        const uint64_t b = frag_offs[f];
-        const uint64_t L = frag_offs[f + 1] - b;
-        const uint64_t nwin = L > (uint64_t)k ? L - k : 0;
-        for (uint64_t base = 0; base < nwin; base += 32) {
-            const uint64_t p = base + lane;
+    auto probe = [&](const Key<NW>& x) {
+        const uint64_t h = filter_hash<NW>(x);
+        const uint32_t fm = filter_bits(h);
+        return (__ldg(&filter[filter_word(h, filter_mask)]) & fm) == fm && (ends_find<NW>(ends, cap_mask, x) & 1u);
+    };
+    // the hits of one step of the warp, placed by one atomic
+    auto record = [&](bool hit, uint64_t p, uint64_t end) {
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
+        if (!m) return;
+        uint64_t first = 0;
+        if (lane == __ffs(m) - 1) first = atomicAdd(n_hits, (unsigned long long)__popc(m));
+        first = __shfl_sync(0xFFFFFFFFu, first, __ffs(m) - 1);
+        if (hit) {
+            const uint64_t idx = first + __popc(m & ((1u << lane) - 1));
+            if (idx < hit_cap) hits[idx] = make_ulonglong2(p, end);
+        }
+    };
+    for (uint64_t g = warp; g * 32 < n_frags; g += n_warps) {
+        const uint64_t f = g * 32 + lane;
+        uint64_t b = 0, nwin = 0;
+        if (f < n_frags) {
+            b = frag_offs[f];
+            const uint64_t L = frag_offs[f + 1] - b;
+            nwin = L > (uint64_t)k ? L - k : 0;
+        }
+        const bool alone = nwin <= (uint64_t)kProbeLaneWindows;
+        const uint64_t mine = alone ? nwin : 0;
+        uint64_t most = mine;
+        for (int off = 16; off; off >>= 1) {
+            const uint64_t o = __shfl_xor_sync(0xFFFFFFFFu, most, off);
+            most = o > most ? o : most;
+        }
+        Key<NW> x{};
+        if (mine) x = load_window<NW>(packed, b, K1);
+        for (uint64_t i = 0; i < most; i++) {
             bool hit = false;
-            if (p < nwin) {
-                const Key<NW> x = load_window<NW>(packed, b + p, K1);
-                const uint64_t h = filter_hash<NW>(x);
-                const uint32_t fm = filter_bits(h);
-                if ((__ldg(&filter[filter_word(h, filter_mask)]) & fm) == fm)
-                    hit = (ends_find<NW>(ends, cap_mask, x) & 1u) != 0;
+            if (i < mine) {
+                if (i) roll_forward<NW>(x, packed_sym(packed, b + i + K1 - 1), K1);
+                hit = probe(x);
             }
-            const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
-            if (!m) continue;
-            uint64_t first = 0;
-            if (lane == __ffs(m) - 1) first = atomicAdd(n_hits, (unsigned long long)__popc(m));
-            first = __shfl_sync(0xFFFFFFFFu, first, __ffs(m) - 1);
-            if (hit) {
-                uint64_t idx = first + __popc(m & ((1u << lane) - 1));
-                if (idx < hit_cap) hits[idx] = make_ulonglong2(b + p, b + nwin);
+            record(hit, b + i, b + mine);
+        }
+        uint32_t big = __ballot_sync(0xFFFFFFFFu, !alone);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const uint64_t fb = __shfl_sync(0xFFFFFFFFu, b, src);
+            const uint64_t fn = __shfl_sync(0xFFFFFFFFu, nwin, src);
+            for (uint64_t base = 0; base < fn; base += 32) {
+                const uint64_t p = base + lane;
+                bool hit = false;
+                if (p < fn) hit = probe(load_window<NW>(packed, fb + p, K1));
+                record(hit, fb + p, fb + fn);
             }
         }
     }
