@@ -16,11 +16,21 @@ constexpr int kMergeThreads = 256;
 
 template <int NW>
 __host__ __device__ constexpr int merge_items() {
-    return 8 / NW;  // 2048, 1024 or 512 keys a CTA: 16 KB of keys
+    return 4 / NW;  // 1024, 512 or 256 keys a CTA: 8 KB of keys
 }
 template <int NW>
 __host__ __device__ constexpr int merge_tile() {
     return kMergeThreads * merge_items<NW>();
+}
+// The set differences stage both inputs' slices and walk twice the merge's
+// items a thread (the tile sizes measured fastest for each).
+template <int NW>
+__host__ __device__ constexpr int diff_items() {
+    return 8 / NW;
+}
+template <int NW>
+__host__ __device__ constexpr int diff_tile() {
+    return kMergeThreads * diff_items<NW>();
 }
 
 // Runs [a, a + na) and [a + na, a + na + nb) merge into [a, a + na + nb) of
@@ -208,7 +218,7 @@ bool merge_runs(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint
 template <int NW>
 __global__ void diff_partition_kernel(const uint64_t* __restrict__ X, uint64_t nx, const uint64_t* __restrict__ Y,
                                       uint64_t ny, uint64_t n_ctas, uint64_t* __restrict__ part) {
-    constexpr int T = merge_tile<NW>();
+    constexpr int T = diff_tile<NW>();
     for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c <= n_ctas;
          c += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t d = c * T < nx + ny ? c * T : nx + ny;
@@ -227,8 +237,8 @@ __global__ void __launch_bounds__(kMergeThreads) diff_kernel(const uint64_t* __r
                                                              uint32_t* __restrict__ tile_counter,
                                                              uint64_t* __restrict__ outX, uint64_t* __restrict__ outY,
                                                              uint32_t* __restrict__ err) {
-    constexpr int ITEMS = merge_items<NW>();
-    constexpr int T = merge_tile<NW>();
+    constexpr int ITEMS = diff_items<NW>();
+    constexpr int T = diff_tile<NW>();
     __shared__ uint64_t sx[T * NW], sy[T * NW];
     __shared__ uint32_t scratch[8];
     __shared__ uint64_t offs[2];
@@ -307,7 +317,7 @@ __global__ void __launch_bounds__(kMergeThreads) diff_kernel(const uint64_t* __r
 template <int NW>
 void set_differences(mh_ctx* ctx, const uint64_t* X, uint64_t nx, const uint64_t* Y, uint64_t ny, uint64_t* outX,
                      uint64_t* n_outX, uint64_t* outY, uint64_t* n_outY) {
-    constexpr int T = merge_tile<NW>();
+    constexpr int T = diff_tile<NW>();
     *n_outX = *n_outY = 0;
     if (nx + ny == 0) return;
     const uint64_t ctas = ceil_div(nx + ny, (uint64_t)T);
