@@ -57,27 +57,17 @@ __global__ void table_index_kernel(const uint64_t* __restrict__ T, uint64_t n, i
 }
 
 // Labels (bit c for label c) of the out-edges of node v in both tables at
-// once: half-warp 0 searches the solid table, half-warp 1 the mercy table.
-// A half reads v.A's bucket 16 entries at a time and finds the first entry
-// >= v.A by a ballot (the bucket's end if none); its lanes 0..3 then read the
-// entries from there (into the next bucket when the index covers the label's
-// bits, for tiny k).  Every lane gets the union of both masks.
+// once: half-warp 0 searches the solid table, half-warp 1 the mercy table,
+// each within [lo, hi), the bucket of v.A in its own table.  A half reads
+// the bucket 16 entries at a time and finds the first entry >= v.A by a
+// ballot (the bucket's end if none); its lanes 0..3 then read the entries
+// from there (into the next bucket when the index covers the label's bits,
+// for tiny k).  Every lane gets the union of both masks.
 template <int NW>
-__device__ __forceinline__ uint32_t out_labels(const uint64_t* __restrict__ S, uint64_t nS,
-                                               const uint64_t* __restrict__ offS, const uint64_t* __restrict__ M,
-                                               uint64_t nM, const uint64_t* __restrict__ offM, int K1, int bits,
+__device__ __forceinline__ uint32_t out_labels(const uint64_t* __restrict__ T, uint64_t n, uint64_t lo, uint64_t hi,
                                                const Key<NW>& v, int lane) {
     const int half = lane >> 4, hl = lane & 15;
-    const uint64_t* T = half ? M : S;
-    const uint64_t n = half ? nM : nS;
-    const uint64_t* off = half ? offM : offS;
     const Key<NW> q = key_shl<NW>(v, 2);
-    uint64_t lo = 0, hi = 0;
-    if (n) {
-        const uint64_t b = top_bits<NW>(q, K1, bits);
-        lo = off[b];
-        hi = off[b + 1];
-    }
     uint64_t pos = hi, base = lo;
     bool done = base >= hi;
     while (__ballot_sync(0xFFFFFFFFu, !done)) {
@@ -109,25 +99,55 @@ __device__ __forceinline__ uint32_t out_labels(const uint64_t* __restrict__ S, u
     return mask;
 }
 
-// One warp per walk (the searches of a step are warp-wide).
+// One warp per walk (the searches of a step are warp-wide).  The bucket of
+// the next step's node does not depend on the label the step picks when the
+// index's bits stop short of the last two symbols (2 K1 - bits >= 4): its
+// bounds are then loaded one step ahead, while this step searches, so that
+// a step waits for one memory access (the bucket) instead of two.
 template <int NW>
 __global__ void walk_kernel(const uint64_t* __restrict__ S, uint64_t nS, const uint64_t* __restrict__ offS,
                             const uint64_t* __restrict__ M, uint64_t nM, const uint64_t* __restrict__ offM,
                             int bits, int k, uint64_t n_walks, uint32_t max_len, uint64_t seed,
-                            uint8_t* __restrict__ slots, uint64_t* __restrict__ lens) {
+                            uint8_t* __restrict__ slots, uint64_t* __restrict__ lens,
+                            unsigned long long* __restrict__ next_walk) {
     const int K1 = k + 1;
     const int lane = threadIdx.x & 31;
     const uint64_t E = nS + nM;
-    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; w < n_walks; w += n_warps) {
+    // this lane's half-warp searches one table
+    const bool mer = (lane >> 4) != 0;
+    const uint64_t* T = mer ? M : S;
+    const uint64_t n = mer ? nM : nS;
+    const uint64_t* off = mer ? offM : offS;
+    const bool ahead = 2 * K1 - bits >= 4;
+    // bounds of the bucket of node v's query v.A
+    auto bucket = [&](const Key<NW>& v, uint64_t& lo, uint64_t& hi) {
+        lo = hi = 0;
+        if (n) {
+            const uint64_t b = top_bits<NW>(key_shl<NW>(v, 2), K1, bits);
+            lo = off[b];
+            hi = off[b + 1];
+        }
+    };
+    // walks are taken one at a time from a counter: walks differ in length
+    // (a dead end ends one early), and a warp that finishes takes the next
+    for (;;) {
+        uint64_t w = 0;
+        if (lane == 0) w = atomicAdd(next_walk, 1ull);
+        w = __shfl_sync(0xFFFFFFFFu, w, 0);
+        if (w >= n_walks) break;
         uint8_t* out = slots + w * max_len;
         const uint64_t s = splitmix64_at(seed, w << 24) % E;
         Key<NW> x = s < nS ? load_key<NW>(S, s) : load_key<NW>(M, s - nS);
         for (int i = lane; i < K1; i += 32) out[i] = "ACGT"[key_sym<NW>(x, K1, i)];
         uint32_t len = K1;
+        Key<NW> v = key_low<NW>(x, 2 * k);
+        uint64_t lo, hi;
+        bucket(v, lo, hi);
         for (uint32_t j = 1; len < max_len; j++) {
-            const Key<NW> v = key_low<NW>(x, 2 * k);
-            const uint32_t mask = out_labels<NW>(S, nS, offS, M, nM, offM, K1, bits, v, lane);
+            // the next node's bucket, for any label (when `ahead`)
+            uint64_t nlo = 0, nhi = 0;
+            if (ahead) bucket(key_low<NW>(key_shl<NW>(v, 2), 2 * k), nlo, nhi);
+            const uint32_t mask = out_labels<NW>(T, n, lo, hi, v, lane);
             if (!mask) break;
             uint32_t r = (uint32_t)(splitmix64_at(seed, (w << 24) + j) % (uint64_t)__popc(mask));
             uint32_t m = mask;
@@ -137,6 +157,13 @@ __global__ void walk_kernel(const uint64_t* __restrict__ S, uint64_t nS, const u
             x.w[0] |= c;
             if (lane == 0) out[len] = "ACGT"[c];
             len++;
+            v = key_low<NW>(x, 2 * k);
+            if (ahead) {
+                lo = nlo;
+                hi = nhi;
+            } else {
+                bucket(v, lo, hi);
+            }
         }
         if (lane == 0) lens[w] = len;
     }
@@ -171,8 +198,11 @@ void walk_contigs(mh_ctx* ctx, const mh_kmers* solid, const mh_kmers* mercy, uin
         if (nM)
             MH_LAUNCH(ctx, "walk_index", grid_for(ctx, nM, 256), 256, 0, table_index_kernel<NW>, mercy->keys, nM,
                       k + 1, bits, offM.p);
+        Buf<uint64_t> next_walk(ctx, 1);
+        next_walk.zero();
         MH_LAUNCH(ctx, "walk", grid_for(ctx, n_walks * 32, 256, 8), 256, 0, walk_kernel<NW>, solid->keys, nS, offS.p,
-                  mercy ? mercy->keys : nullptr, nM, offM.p, bits, k, n_walks, max_len, seed, slots.p, lens.p);
+                  mercy ? mercy->keys : nullptr, nM, offM.p, bits, k, n_walks, max_len, seed, slots.p, lens.p,
+                  (unsigned long long*)next_walk.p);
     }
     exclusive_scan_u64(ctx, lens.p, off.p, n_walks);
     uint64_t total = 0;
