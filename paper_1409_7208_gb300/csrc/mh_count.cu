@@ -7,7 +7,9 @@
 // counts exactly: cnt(x) = cnt(rc x) = run length of canonical(x), doubled
 // when x = rc(x) (a palindrome, counted twice per occurrence).
 //
-//   extract   warp per fragment, window keys from the packed words, canonical
+//   extract   fragments in groups of 32 a warp (a lane per short fragment,
+//             its keys rolled on; a long one by the whole warp), window
+//             keys from the packed words, canonical
 //             (1-word keys: through the invertible mixer mix_bij)
 //   sort      LSD radix over the 2(k+1) key bits; for mixed 1-word keys over
 //             the top ceil(log2 n) + 8 bits plus a fix-up of shared prefixes

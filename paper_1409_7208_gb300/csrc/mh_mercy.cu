@@ -13,7 +13,9 @@
 //   ends     the edges with out0 or in0 (the graph's dead ends, a small
 //            fraction of S) go into a small open-addressing hash table with
 //            their two flags, which stays in L2.
-//   probe    warp per fragment, one window per lane: a test of three bits
+//   probe    fragments in groups of 32 a warp (a lane per short fragment,
+//            its window rolled on; a long fragment by the whole warp, a
+//            window a lane): a test of three bits
 //            of one word in a blocked Bloom filter of the edges without
 //            outdegree (about 8 bits per dead end), and for the few
 //            positives a probe of the small table;
