@@ -9,14 +9,19 @@
 //
 //   extract   fragments in groups of 32 a warp (a lane per short fragment,
 //             its keys rolled on; a long one by the whole warp), window
-//             keys from the packed words, canonical
-//             (1-word keys: through the invertible mixer mix_bij)
-//   sort      LSD radix over the 2(k+1) key bits; for mixed 1-word keys over
-//             the top ceil(log2 n) + 8 bits plus a fix-up of shared prefixes
-//   runs      run heads in a shared-memory bitmask, run lengths from the
-//             next head, solid filter, outputs placed by decoupled look-back
-//   expand    each solid canonical key -> itself and its reverse complement
-//   sort      key-value LSD radix -> solid table in ascending key order
+//             keys from the packed words, canonical, stored as mix_key
+//             images (their top bits evenly spread)
+//   sort      8-bit LSD passes over the top bits only: 3 passes (24 bits)
+//             leave every unit of keys sharing them contiguous
+//   units     each unit sorted and run-length counted on chip by one warp,
+//             the solid filter applied, both strands out (mh_group.cu)
+//   sort      the solid table by the key-value spread sort, ascending
+// The spread route (a plan's alternative): passes over the top ceil(log2 n)
+// bits, a fix-up of keys sharing them, a run pass (runs_kernel: run heads
+// in a shared-memory bitmask, run lengths from the next head, the solid
+// filter, outputs placed by decoupled look-back), the expansion to both
+// strands and the same key-value sort.  Read sets too large for device
+// memory are counted in buckets of the mixed keys' top bits.
 #include <cstdlib>
 #include <vector>
 
@@ -38,10 +43,10 @@ __global__ void frag_windows_kernel(const uint64_t* __restrict__ frag_offs, uint
 constexpr int kLaneWindows = 48;
 
 // Canonical key of every window of every fragment, window i of fragment f
-// written at woff[f] + i (MIXED: as its mix_key image).  With `hist` (1-word keys), the
-// block also counts the digits the sort's passes will use (n_passes digits of
-// rb bits from bit shift0; in dynamic shared memory, added to hist at the
-// end), so the sort needs no histogram pass of its own.
+// written at woff[f] + i (MIXED: as its mix_key image).  With `hist` (1-word
+// keys), the block also counts the digits the sort's passes will use
+// (n_passes digits of rb bits from bit shift0; in dynamic shared memory,
+// added to hist at the end), so the sort needs no histogram pass of its own.
 template <int NW, bool MIXED>
 __global__ void __launch_bounds__(256) extract_canonical_kernel(const uint32_t* __restrict__ packed,
                                                                 const uint64_t* __restrict__ frag_offs,

@@ -59,7 +59,7 @@ struct mh_ctx {
     std::vector<mh_ctx*> workers;        // worker contexts of mh_run_batch (created on first use)
     int sort_shape = -1;                 // scatter tile shape for 1-word keys (-1: default)
     // the counting plan (mh_set_count_plan, or the batch autotuner); defaults: -1 / 0
-    int count_path = -1;                 // 0: unit counting (1-word keys), 1: spread sort, fix-up, run pass
+    int count_path = -1;                 // 0: unit counting, 1: spread sort, fix-up, run pass
     int unit_bits_delta = 0;             // added to the unit bits of the unit counting
     int spread_bits_delta = 0;           // added to the bits the count's spread passes cover (x 8)
     int bucket_bits = -1;                // out-of-core buckets (0..6); -1: the memory plan's choice
