@@ -631,6 +631,28 @@ __global__ void __launch_bounds__(256) unit_compact_kernel(const uint64_t* __res
     }
 }
 
+// The set-aside units between their places in the sorted keys and one
+// contiguous buffer: unit q, keys [list[q].x, list[q].y), is at [off[q],
+// off[q] + its length) of buf.  A warp per unit.
+template <int NW>
+__global__ void __launch_bounds__(256) move_units_kernel(uint64_t* __restrict__ keys,
+                                                         const ulonglong2* __restrict__ list,
+                                                         const uint64_t* __restrict__ off, uint64_t n_list,
+                                                         uint64_t* __restrict__ buf, int to_buf) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t gwarp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t q = gwarp; q < n_list; q += n_warps) {
+        uint64_t* k = keys + list[q].x * NW;
+        uint64_t* b = buf + off[q] * NW;
+        const uint64_t words = (list[q].y - list[q].x) * NW;
+        for (uint64_t t = lane; t < words; t += 32) {
+            if (to_buf) b[t] = k[t];
+            else k[t] = b[t];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ host
 
 static int env_int(const char* name, int dflt) {
@@ -719,11 +741,35 @@ void group_count(mh_ctx* ctx, Buf<uint64_t>& sorted, Buf<uint64_t>& other, uint6
             MH_CUDA(cudaMemcpyAsync(h.data(), deferred.p, sizeof(ulonglong2) * n_def, cudaMemcpyDeviceToHost,
                                     ctx->stream));
             sync_and_check(ctx);
-            for (const ulonglong2& seg : h) {
-                const uint64_t len = seg.y - seg.x;
-                if (radix_sort_spread<NW>(ctx, sorted.p + seg.x * NW, other.p + seg.x * NW, len, skip + ub))
-                    MH_CUDA(cudaMemcpyAsync(sorted.p + seg.x * NW, other.p + seg.x * NW, len * 8 * NW,
-                                            cudaMemcpyDeviceToDevice, ctx->stream));
+            // in key order, so that their concatenation is in unit order
+            std::sort(h.begin(), h.end(), [](const ulonglong2& a, const ulonglong2& b) { return a.x < b.x; });
+            std::vector<uint64_t> off(n_def + 1, 0);
+            for (uint64_t q = 0; q < n_def; q++) off[q + 1] = off[q] + (h[q].y - h[q].x);
+            const uint64_t total = off[n_def];
+            if (n_def > 1 && total <= n / 2) {
+                // many units: gathered into one buffer and sorted there at once
+                // (their top bits order them by unit, so each comes back to its
+                // own range), then moved back
+                MH_CUDA(cudaMemcpyAsync(deferred.p, h.data(), sizeof(ulonglong2) * n_def, cudaMemcpyHostToDevice,
+                                        ctx->stream));
+                Buf<uint64_t> doff(ctx, n_def + 1), g(ctx, total * NW), g2(ctx, total * NW);
+                MH_CUDA(cudaMemcpyAsync(doff.p, off.data(), sizeof(uint64_t) * (n_def + 1), cudaMemcpyHostToDevice,
+                                        ctx->stream));
+                const unsigned mgrid = grid_for(ctx, n_def * 32, 256);
+                MH_LAUNCH(ctx, "move_units", mgrid, 256, 0, move_units_kernel<NW>, sorted.p, deferred.p, doff.p,
+                          n_def, g.p, 1);
+                const bool alt = radix_sort_spread<NW>(ctx, g.p, g2.p, total, skip);
+                MH_LAUNCH(ctx, "move_units", mgrid, 256, 0, move_units_kernel<NW>, sorted.p, deferred.p, doff.p,
+                          n_def, alt ? g2.p : g.p, 0);
+                // the host copies must not be freed before the stream has read them
+                sync_and_check(ctx);
+            } else {
+                for (const ulonglong2& seg : h) {
+                    const uint64_t len = seg.y - seg.x;
+                    if (radix_sort_spread<NW>(ctx, sorted.p + seg.x * NW, other.p + seg.x * NW, len, skip + ub))
+                        MH_CUDA(cudaMemcpyAsync(sorted.p + seg.x * NW, other.p + seg.x * NW, len * 8 * NW,
+                                                cudaMemcpyDeviceToDevice, ctx->stream));
+                }
             }
             MH_LAUNCH(ctx, "sorted_units", grid_for(ctx, n_def * 32, 256), 256, 0, sorted_units_kernel<NW>, sorted.p,
                       deferred.p, n_def, lo, umask, K1, d, other.p, spec_len.p, sk.p, sc.p, ustart.p, ucount.p,

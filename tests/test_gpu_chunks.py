@@ -17,7 +17,8 @@ same way: units too large for a warp's shared memory (counted from global
 memory one distinct key a round, or, with too many distinct keys, set aside,
 sorted by the general radix sort and counted from the sorted keys), one unit
 holding every key, many nearly empty units under three passes, and runs of
-one key thousands of windows long (a read repeated 7,000 times).  The spread
+one key thousands of windows long (a read repeated 7,000 times); and many
+units set aside at once (gathered, sorted together, moved back).  The spread
 path it replaced (passes over the top 32 bits, a fix-up, a run pass) stays
 selectable and is checked as well."""
 import os
@@ -91,5 +92,38 @@ def test_small_input_paths_match_oracle(env):
     full = dict(os.environ, MH_SPREAD_KV_MIN="0")
     full.update(env)
     p = subprocess.run([sys.executable, "-c", CHILD], env=full, capture_output=True, text=True, timeout=900)
+    assert p.returncode == 0, p.stdout + p.stderr
+    assert "ok" in p.stdout
+
+
+SET_ASIDE = r"""
+import sys, numpy as np
+sys.path.insert(0, %r)
+import oracle, synth, paper_1409_7208_gb300 as mh
+k, n_reads = int(sys.argv[1]), int(sys.argv[2])
+ctx = mh.Context(device=0, profile=True)
+# reads of independent random bases: nearly every key distinct, so a unit
+# over the lowered cap has more distinct keys than the global-memory path
+# takes, and is set aside
+ascii, offs = synth.random_reads(11 + k, n_reads, 150, 150)
+reads = mh.mh_pack_reads(ctx, ascii, offs)
+s = mh.mh_count_kmers(ctx, reads, k, 1)
+w = oracle.count(ascii, offs, k, 1, mercy=False)
+gs = s.numpy()
+assert np.array_equal(gs["keys"], w["solid_keys"]) and np.array_equal(gs["counts"], w["solid_cnt"])
+prof = ctx.profile()
+assert prof.get("move_units", (0,))[0] == 2, "the set-aside units were sorted together: %%r" %% sorted(prof)
+print("ok")
+""" % ROOT
+
+
+@pytest.mark.parametrize("k,n_reads,bits,cap", [(31, 6000, 13, 110), (47, 5000, 12, 160), (99, 8000, 12, 130)])
+def test_many_set_aside_units_sorted_together(k, n_reads, bits, cap):
+    """A few per cent of the units over the cap, each with more than 64
+    distinct keys: they are gathered, sorted by one spread sort and moved
+    back (1-, 2- and 4-word keys), and the count equals the oracle's."""
+    env = dict(os.environ, MH_GROUP_UNIT_BITS=str(bits), MH_GROUP_CAP=str(cap))
+    p = subprocess.run([sys.executable, "-c", SET_ASIDE, str(k), str(n_reads)], env=env, capture_output=True,
+                       text=True, timeout=900)
     assert p.returncode == 0, p.stdout + p.stderr
     assert "ok" in p.stdout
