@@ -11,16 +11,17 @@ spectra concatenated, solid tables merged), and reads streamed from host
 memory through staging pieces of 48 bytes or 4 KB (pieces that end inside a
 read, reads that span several pieces, invalid bytes found mid-stream).
 
-The unit counting of 1-word keys (8-bit passes over the top bits, then each
-unit sorted and counted by a warp) is forced through its rarer paths the
+The unit counting (8-bit passes over the top bits, then each unit sorted
+and counted by a warp; the inputs have k = 21 and 31, 47, 99: 1-, 2- and
+4-word keys) is forced through its rarer paths the
 same way: units too large for a warp's shared memory (counted from global
 memory one distinct key a round, or, with too many distinct keys, set aside,
 sorted by the general radix sort and counted from the sorted keys), one unit
 holding every key, many nearly empty units under three passes, and runs of
 one key thousands of windows long (a read repeated 7,000 times); and many
 units set aside at once (gathered, sorted together, moved back).  The spread
-path it replaced (passes over the top 32 bits, a fix-up, a run pass) stays
-selectable and is checked as well."""
+route (passes over the top bits, a fix-up, a run pass) stays selectable and
+is checked as well."""
 import os
 import subprocess
 import sys
