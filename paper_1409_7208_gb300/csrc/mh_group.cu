@@ -12,9 +12,9 @@
 // unit, with no block-wide barrier:
 //
 //   find      the warp streams over a tile of the sorted keys through a
-//             512-key window (256 for 4-word keys) in its shared memory
-//             (filled by asynchronous copies, one round trip for several
-//             units) and finds the units
+//             window of 512 / NW keys in its shared memory (filled by
+//             asynchronous copies, one round trip for several units) and
+//             finds the units
 //             that start in the tile (a unit id is the key's top bits; the
 //             tile's last unit may run past its end)
 //   bucket    a counting sort from the window into the warp's sort buffer by
@@ -33,8 +33,8 @@
 //             more kept outputs, than keys), compacted afterwards in unit
 //             order; the solid table is then sorted.
 //
-// A unit of more than 512 keys (256 of 4 words; keys of very high
-// multiplicity, or many error k-mers in one unit) is counted
+// A unit of more than 512 / NW keys (keys of very high multiplicity, or
+// many error k-mers in one unit) is counted
 // straight from global memory by successive minima: each round the smallest
 // key above the previous one and its multiplicity, one run.  A unit with
 // more than 64 distinct keys as well, or a sub-bucket of more than 32 keys
@@ -57,14 +57,14 @@ constexpr uint32_t kTileKeys = 4096;          // keys a warp's tile holds
 constexpr uint64_t kMaxRounds = 64;           // runs of a large unit counted from global memory
 
 // Per key width: the keys a warp sorts on chip (its window and its sort
-// buffer each hold that many: 4 KB a buffer for 1-word keys, 8 KB for
-// wider ones, whose units are more often large), the warps a CTA, the keys
-// an average unit aims at, and the most an average unit may hold when that
-// saves a pass.
+// buffer each hold that many: 4 KB a buffer; wider keys' units, richer in
+// error k-mers, overflow it more often and are then set aside and sorted
+// together), the warps a CTA, the keys an average unit aims at, and the
+// most an average unit may hold when that saves a pass.
 template <int NW>
 struct UnitCfg {
-    static constexpr int kCap = NW == 4 ? 256 : 512;
-    static constexpr int kWarps = NW == 1 ? 8 : 4;
+    static constexpr int kCap = 512 / NW;
+    static constexpr int kWarps = 8;
     static constexpr int kThreads = 32 * kWarps;
     static constexpr uint64_t kTarget = NW == 1 ? 160 : NW == 2 ? 96 : 56;
     static constexpr uint64_t kMax = NW == 1 ? 256 : NW == 2 ? 160 : 96;
