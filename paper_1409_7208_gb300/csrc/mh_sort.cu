@@ -840,43 +840,35 @@ __global__ void scan_small_kernel(uint64_t* a, uint64_t n) {
     if (threadIdx.x == kScanThreads - 1) a[n] = pre + t;
 }
 
+// Each thread scans its own run of kScanItems consecutive inputs in
+// registers (read and written straight from and to global memory: a warp's
+// runs are one contiguous span), then the block adds the runs' prefixes.
 template <class T>
 __global__ void scan_down_kernel(const T* __restrict__ in, uint64_t n, const uint64_t* __restrict__ offs,
                                  uint64_t* __restrict__ out) {
-    __shared__ uint64_t s[kScanTile];
     __shared__ uint64_t ws[kScanThreads / 32];
-    uint64_t b0 = (uint64_t)blockIdx.x * kScanTile;
-    for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
-        uint64_t idx = b0 + i;
-        s[i] = idx < n ? (uint64_t)in[idx] : 0;
-    }
-    __syncthreads();
+    const uint64_t b = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
     uint64_t loc[kScanItems];
     uint64_t t = 0;
 #pragma unroll
     for (int j = 0; j < kScanItems; j++) {
         loc[j] = t;
-        t += s[threadIdx.x * kScanItems + j];
+        t += b + j < n ? (uint64_t)in[b + j] : 0;
     }
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t x = t;
     for (int off = 1; off < 32; off <<= 1) {
-        uint64_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+        const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
         if (lane >= off) x += y;
     }
     if (lane == 31) ws[warp] = x;
     __syncthreads();
     uint64_t wpre = 0;
     for (int w = 0; w < warp; w++) wpre += ws[w];
-    uint64_t pre = offs[blockIdx.x] + wpre + x - t;
-    __syncthreads();
+    const uint64_t pre = offs[blockIdx.x] + wpre + x - t;
 #pragma unroll
-    for (int j = 0; j < kScanItems; j++) s[threadIdx.x * kScanItems + j] = pre + loc[j];
-    __syncthreads();
-    for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
-        uint64_t idx = b0 + i;
-        if (idx < n) out[idx] = s[i];
-    }
+    for (int j = 0; j < kScanItems; j++)
+        if (b + j < n) out[b + j] = pre + loc[j];
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) out[n] = offs[gridDim.x];
 }
 
