@@ -12,7 +12,10 @@
 //             keys from the packed words, canonical, stored as mix_key
 //             images (their top bits evenly spread)
 //   sort      8-bit LSD passes over the top bits only: 3 passes (24 bits)
-//             leave every unit of keys sharing them contiguous
+//             leave every unit of keys sharing them contiguous.  From 2^22
+//             keys on, the extraction makes the first pass itself: it
+//             writes each tile's keys by digit into fixed-size segments,
+//             and the next pass reads the segments (extract_scatter_kernel)
 //   units     each unit sorted and run-length counted on chip by one warp,
 //             the solid filter applied, both strands out (mh_group.cu)
 //   sort      the solid table by the key-value spread sort, ascending
@@ -22,10 +25,12 @@
 // filter, outputs placed by decoupled look-back), the expansion to both
 // strands and the same key-value sort.  Read sets too large for device
 // memory are counted in buckets of the mixed keys' top bits.
+#include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <vector>
 
-#include "mh_internal.cuh"
+#include "mh_sort_kernels.cuh"
 
 namespace mh {
 
@@ -117,6 +122,171 @@ __global__ void __launch_bounds__(256) extract_canonical_kernel(const uint32_t* 
         for (int i = threadIdx.x; i < nbins; i += blockDim.x)
             if (sh[i]) atomicAdd(&hist[i], sh[i]);
     }
+}
+
+// Extraction fused with the first scatter pass of the unit counting (1-word
+// keys, as mix_key images).  A CTA takes tiles of 256 * ITEMS consecutive
+// windows in turn; a thread computes the keys of ITEMS consecutive windows
+// (the first assembled from the packed words, the others rolled on by one
+// symbol while they stay in one fragment), counts them by the pass's
+// digit (bits [shift, shift + 8)) in its warp's histogram and by the next
+// n_hist passes' digits in the CTA's histogram (added to hist at the end),
+// ranks and stages them in digit order as the scatter pass does, and writes
+// each digit's run to that digit's segment of `out`: segment d is the cap
+// slots from d * cap, and the run's place in it comes from one atomic add
+// on cursor[d] per tile and digit.  The keys of one segment land in no
+// fixed order; they are keys alone, and the later stable passes and the
+// unit sort bring equal keys together whatever that order is.  The digits
+// of mix_key images are close to uniform, so cap is the mean count of a
+// digit with a margin; a run that does not fit is not written and
+// cursor[256] is set, and the caller then takes the unfused path.
+constexpr int kXsTileMax = kSortThreads * 16;
+
+// tfrag[t] = the fragment holding window t * tile (t < n_tiles) or the last
+// window (t = n_tiles): the largest f < F with woff[f] <= that window.
+__global__ void tile_frag_kernel(const uint64_t* __restrict__ woff, uint64_t F, uint64_t n, uint64_t tile,
+                                 uint64_t n_tiles, uint64_t* __restrict__ tfrag) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t <= n_tiles;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t w = t < n_tiles ? t * tile : n - 1;
+        uint64_t lo = 0, hi = F - 1;
+        while (lo < hi) {
+            const uint64_t mid = lo + (hi - lo + 1) / 2;
+            if (woff[mid] <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        tfrag[t] = lo;
+    }
+}
+
+template <int ITEMS, int MINB>
+__global__ void __launch_bounds__(kSortThreads, MINB)
+    extract_scatter_kernel(const uint32_t* __restrict__ packed, const uint64_t* __restrict__ frag_offs,
+                           const uint64_t* __restrict__ woff, const uint64_t* __restrict__ tfrag, uint64_t n, int k,
+                           int shift, int n_hist, uint64_t cap, uint64_t* __restrict__ out,
+                           unsigned long long* __restrict__ cursor, uint32_t* __restrict__ hist) {
+    constexpr int TILE = kSortThreads * ITEMS;
+    __shared__ uint32_t warp_hist[kSortWarps * 256];
+    __shared__ uint32_t ghist[3 * 256];
+    __shared__ uint32_t wsum[kSortWarps];
+    __shared__ uint64_t scatter_base[256];
+    __shared__ uint64_t stage[TILE];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K1 = k + 1;
+    const uint32_t lt_mask = (1u << lane) - 1;
+    for (int i = tid; i < 3 * 256; i += kSortThreads) ghist[i] = 0;
+    const uint64_t n_tiles = ceil_div(n, TILE);
+    uint32_t* wh = warp_hist + warp * 256;
+    for (uint64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        // (the barrier also ends the previous tile's write-out)
+        for (int i = tid; i < kSortWarps * 256; i += kSortThreads) warp_hist[i] = 0;
+        __syncthreads();
+        const uint64_t tb = t * TILE;
+        const uint32_t tile_n = n - tb < (uint64_t)TILE ? (uint32_t)(n - tb) : (uint32_t)TILE;
+        const uint32_t q0 = (uint32_t)tid * ITEMS;
+        uint64_t key[ITEMS];
+#pragma unroll
+        for (int i = 0; i < ITEMS; i++) key[i] = 0;
+        if (q0 < tile_n) {
+            const uint64_t w = tb + q0;
+            uint64_t lo = tfrag[t], hi = tfrag[t + 1];
+            while (lo < hi) {
+                const uint64_t mid = lo + (hi - lo + 1) / 2;
+                if (woff[mid] <= w) lo = mid;
+                else hi = mid - 1;
+            }
+            uint64_t f = lo, wend = woff[f + 1];
+            uint64_t pos = frag_offs[f] + (w - woff[f]);
+            Key<1> x = load_window<1>(packed, pos, K1);
+            Key<1> r = key_rc<1>(x, K1);
+#pragma unroll
+            for (int i = 0; i < ITEMS; i++) {
+                if (i > 0) {
+                    if (q0 + i >= tile_n) break;
+                    if (w + i == wend) {
+                        // the next fragment with windows (empty ones skipped)
+                        do {
+                            f++;
+                        } while (woff[f + 1] == wend);
+                        wend = woff[f + 1];
+                        pos = frag_offs[f];
+                        x = load_window<1>(packed, pos, K1);
+                        r = key_rc<1>(x, K1);
+                    } else {
+                        pos++;
+                        roll_window<1>(x, r, packed_sym(packed, pos + K1 - 1), K1);
+                    }
+                }
+                key[i] = mix_key<1>(key_less<1>(r, x) ? r : x).w[0];
+            }
+        }
+        // counts: the pass's digit per warp, the later passes' per CTA
+#pragma unroll
+        for (int i = 0; i < ITEMS; i++)
+            if (q0 + i < tile_n) {
+                atomicAdd(&wh[(uint32_t)(key[i] >> shift) & 255u], 1u);
+                for (int h = 0; h < n_hist; h++)
+                    atomicAdd(&ghist[h * 256 + ((uint32_t)(key[i] >> (shift + 8 + 8 * h)) & 255u)], 1u);
+            }
+        __syncthreads();
+        const int d = tid;  // kSortThreads == 256
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; w++) {
+            const uint32_t c = warp_hist[w * 256 + d];
+            warp_hist[w * 256 + d] = cnt;
+            cnt += c;
+        }
+        // the digit's places in its segment (awaited only after the ranking)
+        const unsigned long long at = cnt ? atomicAdd(&cursor[d], (unsigned long long)cnt) : 0ull;
+        uint32_t start;
+        {
+            uint32_t x = cnt;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+                if (lane >= off) x += y;
+            }
+            if (lane == 31) wsum[warp] = x;
+            __syncthreads();
+            uint32_t wpre = 0;
+#pragma unroll
+            for (int w = 0; w < kSortWarps; w++) wpre += w < warp ? wsum[w] : 0u;
+            start = wpre + x - cnt;
+        }
+#pragma unroll
+        for (int w = 0; w < kSortWarps; w++) warp_hist[w * 256 + d] += start;
+        __syncthreads();
+        // rank and stage in tile digit order (as the scatter pass does)
+#pragma unroll
+        for (int i = 0; i < ITEMS; i++) {
+            const bool valid = q0 + i < tile_n;
+            const uint32_t dg = valid ? (uint32_t)(key[i] >> shift) & 255u : 256u;
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg);
+            const int leader = __ffs(peers) - 1;
+            uint32_t slot = 0;
+            if (lane == leader && valid) slot = atomicAdd(&wh[dg], (uint32_t)__popc(peers));
+            slot = __shfl_sync(0xFFFFFFFFu, slot, leader) + (uint32_t)__popc(peers & lt_mask);
+            if (valid) stage[slot] = key[i];
+        }
+        const bool fits = at + cnt <= cap;
+        scatter_base[d] = fits ? (uint64_t)d * cap + at - start : ~0ull;
+        if (!fits) cursor[256] = 1ull;
+        __syncthreads();
+        // write out: consecutive staged keys of one digit to consecutive slots
+#pragma unroll
+        for (int i = 0; i < ITEMS; i++) {
+            const uint32_t j = tid + i * kSortThreads;
+            if (j < tile_n) {
+                const uint64_t kk = stage[j];
+                const uint64_t b = scatter_base[(uint32_t)(kk >> shift) & 255u];
+                if (b != ~0ull) out[b + j] = kk;
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < n_hist * 256; i += kSortThreads)
+        if (ghist[i]) atomicAdd(&hist[i], ghist[i]);
 }
 
 // Buckets of the mixed canonical keys: the top `bb` bits of the top word.
@@ -715,6 +885,44 @@ static bool use_unit_count(const mh_ctx* ctx) {
     return ctx->count_path >= 0 ? ctx->count_path == 0 : v;
 }
 
+// The extraction fused with the first pass (extract_scatter_kernel), for
+// 1-word keys sorted by two passes or more, from 2^22 keys on;
+// MH_EXTRACT_SCATTER=0 turns it off, =1 on at any size (tests).
+static bool use_extract_scatter(uint64_t n) {
+    static const int v = [] {
+        const char* e = std::getenv("MH_EXTRACT_SCATTER");
+        return e ? std::atoi(e) : -1;
+    }();
+    return v == 0 ? false : (v == 1 || n >= (1ull << 22));
+}
+
+// Shape of the fused pass (MH_XS_VARIANT): 0 = 14 items a thread and 4
+// CTAs an SM (measured fastest), 1 = (16, 4), 2 = (16, 3), 3 = (12, 5).
+static int xs_variant() {
+    static const int v = [] {
+        const char* e = std::getenv("MH_XS_VARIANT");
+        return e ? std::atoi(e) : 0;
+    }();
+    return v;
+}
+
+// Slots of a segment of the fused pass: the mean count of a digit, plus
+// 1/32 of it and eight standard deviations of a binomial count (the digits
+// of mix_key images are nearly uniform; a k-mer seen m times adds m to one
+// digit, which the 1/32 covers at the coverages met), at least one scatter
+// tile.  MH_SCATTER_CAP sets it (at least a tile): tests make segments
+// overflow with it.
+static uint64_t scatter_cap(uint64_t n) {
+    static const uint64_t forced = [] {
+        const char* e = std::getenv("MH_SCATTER_CAP");
+        return e ? std::strtoull(e, nullptr, 10) : 0ull;
+    }();
+    const uint64_t tile = (uint64_t)std::max(kXsTileMax, sort_tile<1>());
+    if (forced) return std::max(forced, tile);
+    const uint64_t mean = ceil_div(n, 256);
+    return std::max(tile, mean + mean / 32 + 8 * (uint64_t)std::sqrt((double)mean) + 64);
+}
+
 template <int NW>
 void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out) {
     const uint64_t F = reads->n_frags;
@@ -739,22 +947,64 @@ void count_kmers(mh_ctx* ctx, const mh_reads* reads, int k, int d, mh_kmers* out
     if (bb == 0 && use_unit_count(ctx) && gp.passes >= 0) {
         // 8-bit passes over the top bits, then the units sorted and counted
         // by a warp each (mh_group.cu); the extraction counts the passes'
-        // digits for 1-word keys
-        Buf<uint64_t> keys(ctx, (n ? n : 1) * NW), alt(ctx, (n ? n : 1) * NW);
+        // digits for 1-word keys, or (two passes or more) makes the first
+        // pass itself
         const int G = 8 * gp.passes;
-        const bool fuse = NW == 1 && gp.passes > 0;
-        Buf<uint32_t> hist(ctx, fuse ? (size_t)gp.passes * 256 : 1);
-        if (fuse) hist.zero();
-        if (n)
-            MH_LAUNCH_B(ctx, "extract_canonical", reads->n_packed / 4 + n * 8 * NW, grid_for(ctx, F * 32, 256, 8),
-                        256, fuse ? sizeof(uint32_t) * gp.passes * 256 : 0, (extract_canonical_kernel<NW, kMixed>),
-                        reads->packed, reads->frag_offs, woff.p, F, k, keys.p, fuse ? hist.p : nullptr, 64 - G,
-                        gp.passes, 8);
+        Buf<uint64_t> keys, alt;
+        bool in_alt = false, fused = false;
+        if (NW == 1 && n && gp.passes >= 2 && use_extract_scatter(n)) {
+            const uint64_t cap = scatter_cap(n);
+            keys = Buf<uint64_t>(ctx, 256 * cap);
+            alt = Buf<uint64_t>(ctx, n);
+            Buf<unsigned long long> cursor(ctx, 257);
+            Buf<uint32_t> hist(ctx, (size_t)(gp.passes - 1) * 256);
+            cursor.zero();
+            hist.zero();
+            // (items a thread, resident CTAs an SM)
+            static const int shapes[4][2] = {{14, 4}, {16, 4}, {16, 3}, {12, 5}};
+            const int* shape = shapes[xs_variant() & 3];
+            const uint64_t tile = (uint64_t)kSortThreads * shape[0];
+            const uint64_t n_tiles = ceil_div(n, tile);
+            Buf<uint64_t> tfrag(ctx, n_tiles + 1);
+            MH_LAUNCH(ctx, "tile_frag", grid_for(ctx, n_tiles + 1, 256), 256, 0, tile_frag_kernel, woff.p, F, n, tile,
+                      n_tiles, tfrag.p);
+            const unsigned xgrid = (unsigned)std::min<uint64_t>(n_tiles, (uint64_t)ctx->num_sms * shape[1]);
+#define MH_XS_LAUNCH(I, B)                                                                                   \
+    MH_LAUNCH_B(ctx, "extract_scatter", reads->n_packed / 4 + n * 8, xgrid, kSortThreads, 0,                 \
+                (extract_scatter_kernel<I, B>), reads->packed, reads->frag_offs, woff.p, tfrag.p, n, k, 64 - G, \
+                gp.passes - 1, cap, keys.p, cursor.p, hist.p)
+            switch (xs_variant() & 3) {
+                case 1: MH_XS_LAUNCH(16, 4); break;
+                case 2: MH_XS_LAUNCH(16, 3); break;
+                case 3: MH_XS_LAUNCH(12, 5); break;
+                default: MH_XS_LAUNCH(14, 4);
+            }
+#undef MH_XS_LAUNCH
+            uint64_t over = 0;
+            read_u64(ctx, reinterpret_cast<const uint64_t*>(cursor.p) + 256, &over, 1);
+            if (!over) {
+                in_alt = radix_sort_segmented(ctx, keys.p, alt.p, n, cursor.p, cap, 64 - G + 8, 64, hist.p);
+                fused = true;
+            }
+        }
+        if (!fused) {
+            keys.reset();
+            alt.reset();
+            keys = Buf<uint64_t>(ctx, (n ? n : 1) * NW);
+            alt = Buf<uint64_t>(ctx, (n ? n : 1) * NW);
+            const bool fuse = NW == 1 && gp.passes > 0;
+            Buf<uint32_t> hist(ctx, fuse ? (size_t)gp.passes * 256 : 1);
+            if (fuse) hist.zero();
+            if (n)
+                MH_LAUNCH_B(ctx, "extract_canonical", reads->n_packed / 4 + n * 8 * NW,
+                            grid_for(ctx, F * 32, 256, 8), 256, fuse ? sizeof(uint32_t) * gp.passes * 256 : 0,
+                            (extract_canonical_kernel<NW, kMixed>), reads->packed, reads->frag_offs, woff.p, F, k,
+                            keys.p, fuse ? hist.p : nullptr, 64 - G, gp.passes, 8);
+            in_alt = G ? radix_sort<NW>(ctx, keys.p, alt.p, nullptr, nullptr, n, 64 * NW - G, 64 * NW,
+                                        fuse ? hist.p : nullptr)
+                       : false;
+        }
         woff.reset();
-        const bool in_alt =
-            G ? radix_sort<NW>(ctx, keys.p, alt.p, nullptr, nullptr, n, 64 * NW - G, 64 * NW, fuse ? hist.p : nullptr)
-              : false;
-        hist.reset();
         Buf<uint64_t>& sorted = in_alt ? alt : keys;
         Buf<uint64_t>& other = in_alt ? keys : alt;
         Buf<uint64_t> sk;

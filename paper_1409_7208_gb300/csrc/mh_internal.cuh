@@ -668,6 +668,13 @@ __device__ __forceinline__ uint64_t key_hash(const Key<NW>& a) {
 template <int NW>
 bool radix_sort(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt, uint64_t n,
                 int bit_lo, int bit_hi, const uint32_t* hist = nullptr);
+// The same for n 1-word keys held in 256 segments of seg_cap slots each
+// (segment r's seg_cnt[r] keys at r * seg_cap; seg_cap at least one scatter
+// tile): the first pass reads the segments, and every pass writes n
+// contiguous keys.  `hist` is required.
+bool radix_sort_segmented(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n,
+                          const unsigned long long* seg_cnt, uint64_t seg_cap, int bit_lo, int bit_hi,
+                          const uint32_t* hist);
 
 // Sort of mix_key images (evenly spread top bits): LSD passes over the top
 // P = spread_pass_bits(n) bits below the top `skip` bits (equal in every

@@ -153,7 +153,7 @@ static int sort_noalloc(const uint64_t* in, uint64_t* out, uint64_t n, int key_b
         MH_TRY(cudaMemsetAsync(counter, 0, sizeof(uint32_t), st));
         onesweep_kernel<NW, false><<<(unsigned)tiles, kSortThreads, smem, st>>>(
             src, dst, nullptr, nullptr, n, 8 * p, base + (uint64_t)p * 256, nullptr, status, counter, err,
-            kSpinLimit, 0);
+            kSpinLimit, 0, SegIn{});
         MH_TRY(cudaGetLastError());
         src = dst;
     }

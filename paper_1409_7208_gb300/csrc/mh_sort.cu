@@ -13,7 +13,10 @@
 // so a pass runs in chunks of at most (2^18 - 1) tiles, one launch per chunk,
 // each with its own look-back chain.  Chunk 0 starts from the global digit
 // offsets of the histogram (the same for every pass); the last tile of chunk
-// c writes the digit offsets where chunk c+1 starts.
+// c writes the digit offsets where chunk c+1 starts.  The first pass may
+// read a segmented input (radix_sort_segmented: the keys of each value of
+// the previous digit in a segment of fixed size, as the fused extraction
+// of mh_count.cu writes them); its tiles then skip the unused slots.
 #include <atomic>
 #include <cstdlib>
 #include <vector>
@@ -59,25 +62,29 @@ static int take_withhold() {
     return v > 0 ? 1 : 0;
 }
 
+// seg.cnt set: the first pass reads a segmented input of 256 * seg.cap
+// slots holding the n keys (SegIn); every pass writes n contiguous keys.
 template <int NW, bool HV, int ITEMS, int MINB>
 static bool radix_sort_impl(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt, uint64_t n,
-                            int bit_lo, int bit_hi, const uint32_t* hist_in) {
+                            int bit_lo, int bit_hi, const uint32_t* hist_in, SegIn seg = SegIn{}) {
     if (n <= 1 || bit_hi <= bit_lo) return false;
     constexpr int TILE = sort_tile<NW, ITEMS>();
     const int n_passes = (bit_hi - bit_lo + 7) / 8;
     const uint64_t chunk_len = chunk_tiles() * TILE;
-    const int n_chunks = (int)ceil_div(n, chunk_len);
+    // positions pass p reads: the segment slots in the first pass
+    auto span = [&](int p) { return p == 0 && seg.cnt ? 256 * seg.cap : n; };
+    const int max_chunks = (int)ceil_div(span(0), chunk_len);
     Buf<uint32_t> hist(ctx, hist_in ? 1 : (size_t)n_passes * 256);
-    // base[(p * n_chunks + c) * 256 + d]: where chunk c of pass p starts writing digit d
-    Buf<uint64_t> base(ctx, (size_t)n_passes * n_chunks * 256);
+    // base[(p * max_chunks + c) * 256 + d]: where chunk c of pass p starts writing digit d
+    Buf<uint64_t> base(ctx, (size_t)n_passes * max_chunks * 256);
     if (!hist_in) {
         hist.zero();
         MH_LAUNCH_B(ctx, "radix_hist", n * 8 * NW, grid_for(ctx, n, 256, 8), 256, sizeof(uint32_t) * n_passes * 256,
                     radix_hist_kernel<NW>, keys, n, bit_lo, n_passes, hist.p);
     }
     MH_LAUNCH(ctx, "radix_base", n_passes, 256, 0, radix_base_kernel, hist_in ? hist_in : hist.p, base.p,
-              (uint64_t)n_chunks * 256);
-    const uint64_t max_tiles = std::min<uint64_t>(chunk_tiles(), ceil_div(n, TILE));
+              (uint64_t)max_chunks * 256);
+    const uint64_t max_tiles = std::min<uint64_t>(chunk_tiles(), ceil_div(span(0), TILE));
     Buf<uint32_t> status(ctx, max_tiles * 256);
     Buf<uint32_t> counter(ctx, 64);
     constexpr size_t smem = onesweep_smem<NW, HV, ITEMS>();
@@ -86,17 +93,32 @@ static bool radix_sort_impl(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t
     uint64_t *kin = keys, *kout = alt;
     uint32_t *vin = vals, *vout = valt;
     for (int p = 0; p < n_passes; p++) {
+        const uint64_t np = span(p);
+        const int n_chunks = (int)ceil_div(np, chunk_len);
         for (int c = 0; c < n_chunks; c++) {
             uint64_t c0 = (uint64_t)c * chunk_len;
-            uint64_t len = std::min(chunk_len, n - c0);
+            uint64_t len = std::min(chunk_len, np - c0);
             uint64_t tiles = ceil_div(len, TILE);
             MH_CUDA(cudaMemsetAsync(status.p, 0, tiles * 256 * sizeof(uint32_t), ctx->stream));
             MH_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(uint32_t), ctx->stream));
+            uint64_t* nb = c + 1 < n_chunks ? base.p + ((uint64_t)p * max_chunks + c + 1) * 256 : nullptr;
+            if constexpr (NW == 1 && !HV) {
+                if (p == 0 && seg.cnt) {
+                    SegIn sp = seg;
+                    sp.slot0 = c0;
+                    MH_CUDA(cudaFuncSetAttribute(onesweep_kernel<NW, HV, ITEMS, MINB, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                    MH_LAUNCH_B(ctx, "radix_onesweep", len * 16, (unsigned)tiles, kSortThreads, smem,
+                                (onesweep_kernel<NW, HV, ITEMS, MINB, true>), kin + c0, kout, nullptr, nullptr, len,
+                                bit_lo, base.p + (uint64_t)c * 256, nb, status.p, counter.p, ctx->d_status,
+                                spin_limit(), take_withhold(), sp);
+                    continue;
+                }
+            }
             MH_LAUNCH_B(ctx, "radix_onesweep", len * (16 * NW + (HV ? 8 : 0)), (unsigned)tiles, kSortThreads, smem,
                         (onesweep_kernel<NW, HV, ITEMS, MINB>), kin + c0 * NW, kout, HV ? vin + c0 : nullptr, vout, len,
-                        bit_lo + 8 * p, base.p + ((uint64_t)p * n_chunks + c) * 256,
-                        c + 1 < n_chunks ? base.p + ((uint64_t)p * n_chunks + c + 1) * 256 : nullptr, status.p,
-                        counter.p, ctx->d_status, spin_limit(), take_withhold());
+                        bit_lo + 8 * p, base.p + ((uint64_t)p * max_chunks + c) * 256, nb, status.p, counter.p,
+                        ctx->d_status, spin_limit(), take_withhold(), SegIn{});
         }
         std::swap(kin, kout);
         std::swap(vin, vout);
@@ -119,19 +141,29 @@ static int sort_variant() {
 
 template <int NW, bool HV>
 static bool radix_sort_dispatch(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint32_t* vals, uint32_t* valt,
-                                uint64_t n, int bit_lo, int bit_hi, const uint32_t* h) {
+                                uint64_t n, int bit_lo, int bit_hi, const uint32_t* h, SegIn seg = SegIn{}) {
     if constexpr (NW == 1) {
         if constexpr (HV) {
-            return radix_sort_impl<NW, HV, 14, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h);
+            return radix_sort_impl<NW, HV, 14, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h, seg);
         } else {
             switch (ctx->sort_shape >= 0 ? ctx->sort_shape : sort_variant()) {
-                case 1: return radix_sort_impl<NW, HV, 12, 4>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h);
-                case 2: return radix_sort_impl<NW, HV, 14, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h);
-                default: return radix_sort_impl<NW, HV, 16, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h);
+                case 1: return radix_sort_impl<NW, HV, 12, 4>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h, seg);
+                case 2: return radix_sort_impl<NW, HV, 14, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h, seg);
+                default: return radix_sort_impl<NW, HV, 16, 3>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h, seg);
             }
         }
     }
-    return radix_sort_impl<NW, HV, SortItems<NW>::v, 2>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h);
+    return radix_sort_impl<NW, HV, SortItems<NW>::v, 2>(ctx, keys, alt, vals, valt, n, bit_lo, bit_hi, h, seg);
+}
+
+bool radix_sort_segmented(mh_ctx* ctx, uint64_t* keys, uint64_t* alt, uint64_t n,
+                          const unsigned long long* seg_cnt, uint64_t seg_cap, int bit_lo, int bit_hi,
+                          const uint32_t* hist) {
+    if (seg_cap < (uint64_t)sort_tile<1>() || !hist) throw Error{MH_EINVAL, "segmented sort: bad segments"};
+    SegIn seg;
+    seg.cnt = seg_cnt;
+    seg.cap = seg_cap;
+    return radix_sort_dispatch<1, false>(ctx, keys, alt, nullptr, nullptr, n, bit_lo, bit_hi, hist, seg);
 }
 
 template <int NW>

@@ -90,13 +90,23 @@ static __global__ void radix_base_kernel(const uint32_t* __restrict__ hist, uint
 }
 
 // --------------------------------------------------------------- onesweep
-template <int NW, bool HV, int ITEMS = SortItems<NW>::v, int MINB = 2>
+// A segmented input (SEG): the slots [r * cap, r * cap + cnt[r]) hold
+// segment r's keys and the rest of the slots are unused.  Slot 0 of the
+// launch is slot slot0 of the whole input; cap is at least one tile, so a
+// tile meets at most two segments.
+struct SegIn {
+    const unsigned long long* cnt = nullptr;
+    uint64_t cap = 0;
+    uint64_t slot0 = 0;
+};
+
+template <int NW, bool HV, int ITEMS = SortItems<NW>::v, int MINB = 2, bool SEG = false>
 __global__ void __launch_bounds__(kSortThreads, MINB)
     onesweep_kernel(const uint64_t* __restrict__ kin, uint64_t* __restrict__ kout, const uint32_t* __restrict__ vin,
                     uint32_t* __restrict__ vout, uint64_t n, int shift, const uint64_t* __restrict__ digit_base,
                     uint64_t* __restrict__ next_base, uint32_t* __restrict__ status,
                     uint32_t* __restrict__ tile_counter, uint32_t* __restrict__ err, int spin_limit,
-                    int withhold_first) {
+                    int withhold_first, SegIn seg) {
     constexpr int TILE = sort_tile<NW, ITEMS>();
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* warp_hist = reinterpret_cast<uint32_t*>(smem);          // [warps][256]
@@ -113,7 +123,24 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
     const uint64_t tile_base = (uint64_t)tile * TILE;
     const uint64_t rem = n - tile_base;
     const uint32_t tile_n = rem < (uint64_t)TILE ? (uint32_t)rem : (uint32_t)TILE;
-    const bool full = tile_n == (uint32_t)TILE;
+    // the tile's keys: positions [0, va) and [vb, vc) (one run unless the
+    // input is segmented and the tile crosses into the next segment)
+    uint32_t va = tile_n, vb = TILE, vc = TILE;
+    if constexpr (SEG) {
+        const uint64_t s = seg.slot0 + tile_base;
+        const uint64_t r0 = s / seg.cap;
+        const uint64_t e0 = r0 * seg.cap + seg.cnt[r0];
+        va = e0 > s ? (uint32_t)(e0 - s < (uint64_t)tile_n ? e0 - s : tile_n) : 0u;
+        const uint64_t nb = (r0 + 1) * seg.cap - s;
+        if (nb < tile_n) {
+            vb = (uint32_t)nb;
+            const uint64_t e1 = nb + seg.cnt[r0 + 1];
+            vc = (uint32_t)(e1 < (uint64_t)tile_n ? e1 : tile_n);
+        }
+    }
+    const bool full = SEG ? va == (uint32_t)TILE : tile_n == (uint32_t)TILE;
+    const uint32_t n_valid = SEG ? va + (vc - vb) : tile_n;
+#define MH_PRESENT(q) (SEG ? ((q) < va || (q) - vb < vc - vb) : ((q) < tile_n))
     const uint64_t* kt = kin + tile_base * NW;
     const uint32_t* vt = HV ? vin + tile_base : nullptr;
 
@@ -130,7 +157,7 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
     } else {
 #pragma unroll
         for (int i = 0; i < ITEMS; i++) {
-            if (w0 + 32 * i < tile_n) {
+            if (MH_PRESENT(w0 + 32 * i)) {
                 k[i] = load_key<NW>(kt, w0 + 32 * i);
                 if constexpr (HV) v[i] = vt[w0 + 32 * i];
             } else {
@@ -145,7 +172,7 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
     const uint32_t lt_mask = (1u << lane) - 1;
 #pragma unroll
     for (int i = 0; i < ITEMS; i++)
-        if (full || (w0 + 32 * i < tile_n)) atomicAdd(&wh[key_digit<NW>(k[i], shift)], 1u);
+        if (full || MH_PRESENT(w0 + 32 * i)) atomicAdd(&wh[key_digit<NW>(k[i], shift)], 1u);
     __syncthreads();
     // per digit: exclusive prefix over warps, tile total
     const int d = tid;  // kSortThreads == 256
@@ -189,7 +216,7 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
     // is done the earlier tiles have published more of theirs.
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
-        const bool valid = full || (w0 + 32 * i < tile_n);
+        const bool valid = full || MH_PRESENT(w0 + 32 * i);
         const uint32_t dg = valid ? key_digit<NW>(k[i], shift) : 256u;
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg);
         const int leader = __ffs(peers) - 1;
@@ -235,7 +262,7 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
 #pragma unroll
     for (int i = 0; i < ITEMS; i++) {
         const uint32_t j = tid + i * kSortThreads;
-        if (full || j < tile_n) {
+        if (full || j < n_valid) {
             Key<NW> kk;
 #pragma unroll
             for (int w = 0; w < NW; w++) kk.w[w] = stage[w * TILE + j];
@@ -245,5 +272,6 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
         }
     }
 }
+#undef MH_PRESENT
 
 }  // namespace mh

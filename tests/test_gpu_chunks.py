@@ -87,7 +87,11 @@ print("ok")
     {"MH_GROUP_UNIT_BITS": "14"}, {"MH_GROUP_UNIT_BITS": "22", "MH_SORT_CHUNK_TILES": "3"},
     {"MH_COUNT_BUCKET_BITS": "1"}, {"MH_COUNT_BUCKET_BITS": "4"},
     {"MH_COUNT_BUCKET_BITS": "4", "MH_COUNT_PATH": "spread"}, {"MH_SPREAD_KV_MIN": "0"},
-    {"MH_PACK_PIECE": "48"}, {"MH_PACK_PIECE": "4096"}], ids=lambda e: ",".join("%s=%s" % kv for kv in e.items()))
+    {"MH_PACK_PIECE": "48"}, {"MH_PACK_PIECE": "4096"},
+    {"MH_EXTRACT_SCATTER": "1"}, {"MH_EXTRACT_SCATTER": "1", "MH_SORT_CHUNK_TILES": "1"},
+    {"MH_EXTRACT_SCATTER": "1", "MH_SORT_VARIANT": "1"},
+    {"MH_EXTRACT_SCATTER": "1", "MH_SCATTER_CAP": "5000", "MH_GROUP_UNIT_BITS": "22", "MH_SORT_CHUNK_TILES": "3"}],
+    ids=lambda e: ",".join("%s=%s" % kv for kv in e.items()))
 def test_small_input_paths_match_oracle(env):
     # every run also sorts the small solid tables by the spread key-value path
     full = dict(os.environ, MH_SPREAD_KV_MIN="0")
@@ -125,6 +129,45 @@ def test_many_set_aside_units_sorted_together(k, n_reads, bits, cap):
     back (1-, 2- and 4-word keys), and the count equals the oracle's."""
     env = dict(os.environ, MH_GROUP_UNIT_BITS=str(bits), MH_GROUP_CAP=str(cap))
     p = subprocess.run([sys.executable, "-c", SET_ASIDE, str(k), str(n_reads)], env=env, capture_output=True,
+                       text=True, timeout=900)
+    assert p.returncode == 0, p.stdout + p.stderr
+    assert "ok" in p.stdout
+
+
+FUSED = r"""
+import sys, numpy as np
+sys.path.insert(0, %r)
+import oracle, synth, paper_1409_7208_gb300 as mh
+n_reads, expect = int(sys.argv[1]), sys.argv[2].split(",")
+ctx = mh.Context(device=0, profile=True)
+ascii, offs = synth.metagenome_reads(seed=9, n_genomes=20, median_len=2e5, n_pairs=n_reads // 2)
+reads = mh.mh_pack_reads(ctx, ascii, offs)
+s = mh.mh_count_kmers(ctx, reads, 31, 2)
+w = oracle.count(ascii, offs, 31, 2, mercy=False)
+gs = s.numpy()
+assert np.array_equal(gs["keys"], w["solid_keys"]) and np.array_equal(gs["counts"], w["solid_cnt"])
+prof = ctx.profile()
+for name in expect:
+    assert (name[1:] not in prof) if name.startswith("-") else (name in prof), (name, sorted(prof))
+print("ok")
+""" % ROOT
+
+
+@pytest.mark.parametrize("n_reads,env,expect", [
+    (4000, {"MH_EXTRACT_SCATTER": "1"}, "extract_scatter,-extract_canonical"),
+    (12000, {"MH_EXTRACT_SCATTER": "1"}, "extract_scatter,-extract_canonical"),
+    (12000, {"MH_EXTRACT_SCATTER": "1", "MH_SCATTER_CAP": "4096"}, "extract_scatter,extract_canonical"),
+    (12000, {"MH_EXTRACT_SCATTER": "0"}, "-extract_scatter,extract_canonical")])
+def test_extraction_fused_with_first_pass(n_reads, env, expect):
+    """The extraction that makes the first 8-bit pass itself (keys written
+    to fixed-size digit segments, then a pass that reads the segments):
+    the count equals the oracle's, with the fused kernel in place of the
+    plain extraction; with segments too small for their digits (more than
+    4,096 keys a digit: 12,000 reads of 150 bp give 1.43 M keys) the
+    overflow is caught and the unfused path gives the same count."""
+    full = dict(os.environ)
+    full.update(env)
+    p = subprocess.run([sys.executable, "-c", FUSED, str(n_reads), expect], env=full, capture_output=True,
                        text=True, timeout=900)
     assert p.returncode == 0, p.stdout + p.stderr
     assert "ok" in p.stdout
