@@ -261,8 +261,8 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
 #pragma unroll
         for (int i = 0; i < ITEMS; i++) {
             const bool valid = q0 + i < tile_n;
-            const uint32_t dg = valid ? (uint32_t)(key[i] >> shift) & 255u : 256u;
-            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg);
+            const uint32_t dg = (uint32_t)(key[i] >> shift) & 255u;
+            const uint32_t peers = digit_peers(dg) & (__ballot_sync(0xFFFFFFFFu, valid) | (1u << lane));
             const int leader = __ffs(peers) - 1;
             uint32_t slot = 0;
             if (lane == leader && valid) slot = atomicAdd(&wh[dg], (uint32_t)__popc(peers));

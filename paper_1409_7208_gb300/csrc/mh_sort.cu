@@ -5,7 +5,7 @@
 // single read of the keys; then each pass is one "onesweep" kernel: a CTA
 // takes the next tile (dynamic tile id, so every earlier tile already runs),
 // counts its keys' digits in per-warp shared-memory histograms, publishes
-// the tile's per-digit counts, ranks the keys by digit with warp match and
+// the tile's per-digit counts, ranks the keys by digit with warp ballots and
 // one shared atomic per group of equal digits (stable: rank follows input
 // order) while staging them in shared memory in digit order, looks back
 // over earlier tiles' published counts (decoupled look-back, every wait
