@@ -5,12 +5,12 @@
 // single read of the keys; then each pass is one "onesweep" kernel: a CTA
 // takes the next tile (dynamic tile id, so every earlier tile already runs),
 // counts its keys' digits in per-warp shared-memory histograms, publishes
-// the tile's per-digit counts, ranks the keys by digit with warp ballots and
-// one shared atomic per group of equal digits (stable: rank follows input
-// order) while staging them in shared memory in digit order, looks back
-// over earlier tiles' published counts (decoupled look-back, every wait
-// bounded) and writes the tile out in coalesced runs.  Look-back counts are 30-bit,
-// so a pass runs in chunks of at most (2^18 - 1) tiles, one launch per chunk,
+// the tile's per-digit counts, ranks the keys by digit (a warp match on the
+// digit's top bits, ballots on the rest) with one shared atomic per group of
+// equal digits (stable: rank follows input order) while staging them in
+// shared memory in digit order, looks back over earlier tiles' published
+// counts (decoupled look-back, every wait bounded) and writes the tile out
+// in coalesced runs.  Look-back counts are 30-bit, so a pass runs in chunks of at most (2^18 - 1) tiles, one launch per chunk,
 // each with its own look-back chain.  Chunk 0 starts from the global digit
 // offsets of the histogram (the same for every pass); the last tile of chunk
 // c writes the digit offsets where chunk c+1 starts.  The first pass may

@@ -89,16 +89,18 @@ static __global__ void radix_base_kernel(const uint32_t* __restrict__ hist, uint
     base[p * base_stride + d] = s[d] - tot;
 }
 
-// The lanes of the warp whose digit (8 bits) equals this lane's: one ballot
-// per bit, each keeping the lanes that agree with this lane on that bit.
-// A warp match instruction would give the same set, but it occupies the
-// SM's divergence unit for about one cycle per distinct value in the warp
-// (some 30 for random digits), and that unit, shared by the SM, became
-// the scatter pass's bottleneck; the ballots are ordinary instructions.
+// The lanes of the warp whose digit (8 bits) equals this lane's.  A warp
+// match instruction finds such sets, but it runs on the SM's divergence
+// unit, one per SM, for about one cycle per distinct value among the lanes:
+// on a whole random digit (some 30 values) that unit bound the scatter
+// pass.  So the match takes the top kMatchBits bits only (at most 8
+// values), and one ballot per remaining bit keeps the lanes that agree
+// with this lane on that bit (ordinary instructions).
+constexpr int kMatchBits = 3;
 __device__ __forceinline__ uint32_t digit_peers(uint32_t dg) {
-    uint32_t peers = 0xFFFFFFFFu;
+    uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg >> (8 - kMatchBits));
 #pragma unroll
-    for (int b = 0; b < 8; b++) {
+    for (int b = 0; b < 8 - kMatchBits; b++) {
         const uint32_t bit = (dg >> b) & 1u;
         const uint32_t bal = __ballot_sync(0xFFFFFFFFu, bit);
         peers &= bit ? bal : ~bal;
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(kSortThreads, MINB)
     for (int w = 0; w < kSortWarps; w++) warp_hist[w * 256 + d] += start;
     __syncthreads();
     // rank and stage in tile digit order, stable by item then lane: the
-    // lanes holding one digit in one item find each other (ballots), the
+    // lanes holding one digit in one item find each other (digit_peers), the
     // lowest of them takes their slots from the warp's counter in one
     // atomic add and hands the first slot on; each lane adds the number of
     // its lower peers.  Staging needs no global prefix, and by the time it
